@@ -1,0 +1,182 @@
+/*
+ * irk_gb300.h -- C ABI of the GB300 (sm_103a) stage-system solver.
+ *
+ * One call of irk_factor + irk_solve performs the per-time-step linear solve
+ * of a fully implicit s-stage Runge-Kutta method applied to a discontinuous
+ * Galerkin semi-discretisation M du/dt = f(u) (Pazner & Persson,
+ * arXiv 1701.07181):
+ *
+ *     B W = R,   B = A^{-1} (x) M - dt (I_s (x) J)          (Sec. 4.3, eq. big-irk)
+ *
+ * (the "transformed" system of Sec. 4.1, eq. modified-IRK), or optionally the
+ * untransformed system (I_s (x) M - dt (A (x) J)) K = R (Sec. 4.1,
+ * eq. newton-system-2), by restarted flexible GMRES (Sec. 4) preconditioned
+ * with block ILU(0) (Sec. 4.2-4.3).  The new step is u1 = u0 + dt w_s
+ * (Sec. 4.1: b^T A^{-1} = e_s^T for Radau IIA).
+ *
+ * Notation (Sec. 2.1): T elements, m unknowns per element, n = T m; J is a
+ * T x T block matrix of dense m x m blocks (diagonal + one block per face
+ * neighbour), M is block diagonal.
+ *
+ * Data layout at this boundary (all row-major, all double):
+ *   row_ptr[T+1], col_idx[nnzb]  block-CSR pattern of J, int32, columns sorted
+ *                                ascending within a row, diagonal present.
+ *   J[nnzb*m*m]                  blocks of J in pattern order, each m x m
+ *                                row-major.
+ *   M[T*m*m]                     diagonal blocks of M, each m x m row-major.
+ *   R, W[s*T*m]                  stage vectors stacked stage-major:
+ *                                X[(k*T + i)*m + a] = component a of element
+ *                                i of stage k (the stacking of Sec. 4.1).
+ *
+ * Memory spaces: every pointer argument that carries data is in the memory
+ * space given by the call's mem_space argument (IRK_HOST: host memory, the
+ * library copies through its own staging; IRK_DEVICE: device memory of the
+ * context's GPU).  The caller keeps ownership of every buffer it passes; the
+ * library copies inputs into buffers it owns and writes outputs into the
+ * caller's buffers.  No pointer is retained after a call returns.
+ *
+ * Errors: every int-returning call returns IRK_OK (0), IRK_NOT_CONVERGED (1,
+ * a result is still written), or a negative IRK_ERR_* code; irk_strerror
+ * gives a message.  A context is not thread safe; distinct contexts are
+ * independent.  All work of a context is ordered on the stream in its options
+ * (NULL = the legacy default stream); calls return after that work completed.
+ */
+#ifndef IRK_GB300_H
+#define IRK_GB300_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define IRK_API __attribute__((visibility("default")))
+#else
+#define IRK_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct irk_ctx irk_ctx;
+
+enum irk_status {
+    IRK_OK = 0,
+    IRK_NOT_CONVERGED = 1, /* max_iter reached; best iterate written */
+    IRK_ERR_INVALID = -1,  /* bad argument or pattern */
+    IRK_ERR_NOMEM = -2,    /* device or host allocation failed */
+    IRK_ERR_SINGULAR = -3, /* zero pivot in a diagonal block of the ILU(0) */
+    IRK_ERR_NONFINITE = -4,/* NaN/Inf in a residual or Krylov quantity */
+    IRK_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
+    IRK_ERR_CUDA = -6,     /* a CUDA runtime call failed */
+    IRK_ERR_STATE = -7     /* call out of order (e.g. apply before factor) */
+};
+
+enum irk_mem_space { IRK_HOST = 0, IRK_DEVICE = 1 };
+
+/* Preconditioners (Sec. 4.3). */
+enum irk_precond_kind {
+    IRK_PC_NONE = 0,
+    /* Sec. 4.3.2: s independent block ILU(0) factors of
+     * (A^{-1}_kk + alpha_k) M - dt J, applied to all stages at once. */
+    IRK_PC_UNCOUPLED = 1,
+    /* Sec. 4.3.1, Alg. 3: block ILU(0) of the whole system with the
+     * unknowns ordered stage-major (stage, element). */
+    IRK_PC_COUPLED = 2,
+    /* block ILU(0) of the whole system ordered element-major, with one
+     * (s m) x (s m) block per element pair (any formulation). */
+    IRK_PC_ELEMENT = 3
+};
+
+/* Storage / arithmetic precision of the ILU(0) factors and sweeps. */
+enum irk_factor_precision { IRK_FACTOR_FP64 = 0, IRK_FACTOR_FP32 = 1, IRK_FACTOR_BF16 = 2 };
+
+/* Arithmetic of the outer Krylov method (operator product, Gram-Schmidt,
+ * residuals).  FP64: IEEE binary64 on the FP64 pipe.  DF64: double-float
+ * (pairs of binary32 with error-free transformations, about 48 significant
+ * bits) on the FP32 pipe, which GB300 executes about 60x faster. */
+enum irk_krylov_arith { IRK_KRYLOV_FP64 = 0, IRK_KRYLOV_DF64 = 1 };
+
+enum irk_formulation { IRK_TRANSFORMED = 0, IRK_UNTRANSFORMED = 1 };
+
+typedef struct {
+    int restart;       /* GMRES restart length (default 30) */
+    int max_iter;      /* total inner iterations (default 3000) */
+    int precond;       /* enum irk_precond_kind (default IRK_PC_UNCOUPLED) */
+    int factor_prec;   /* enum irk_factor_precision (default IRK_FACTOR_FP64) */
+    int krylov_arith;  /* enum irk_krylov_arith (default IRK_KRYLOV_FP64) */
+    int formulation;   /* enum irk_formulation (default IRK_TRANSFORMED) */
+    const double *shift; /* host array of s shifts alpha_k for IRK_PC_UNCOUPLED;
+                            NULL = alpha_k = sum_{j != k} |A^{-1}_jk| (Sec. 4.3.2);
+                            copied at irk_setup */
+    void *stream;      /* cudaStream_t for all work of the context; NULL = default */
+    int timing;        /* 1: time each phase of irk_factor / irk_solve with CUDA
+                          events on the context's stream (see irk_stats); default 0 */
+} irk_options;
+
+/* Fill *opt with the defaults listed above. */
+IRK_API void irk_default_options(irk_options *opt);
+
+/* Create a context for one stage system (Sec. 4.1, eq. big-irk).
+ *   s         number of stages, 1 <= s <= 8.
+ *   A         host s*s row-major Butcher matrix, invertible; NULL = Radau IIA
+ *             with s stages (App. A; computed by collocation).
+ *   T, m      elements and block size, T >= 1, 1 <= m <= 128.
+ *   row_ptr, col_idx, J, M   as in the layout notes above, in mem_space.
+ *   opt       NULL = defaults.  The pattern must be structurally symmetric.
+ * Copies everything; allocates the Krylov workspace for the given restart.
+ * Returns IRK_ERR_INVALID for a malformed pattern (unsorted, missing
+ * diagonal, out-of-range column, not symmetric). */
+IRK_API int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t *row_ptr,
+              const int32_t *col_idx, const double *J, const double *M, int mem_space,
+              const irk_options *opt);
+
+/* Replace the values of J and M (same pattern), e.g. at a new Newton
+ * iterate (Sec. 4.1).  Invalidates the factors. */
+IRK_API int irk_update_values(irk_ctx *ctx, const double *J, const double *M, int mem_space);
+
+/* Build the preconditioner for time step dt (once per linear solve,
+ * Sec. 4.4): assemble the system blocks and compute their block ILU(0)
+ * (Alg. 2 / Alg. 3 / textbook form), level by level.  IRK_ERR_SINGULAR if a
+ * diagonal block has a zero pivot. */
+IRK_API int irk_factor(irk_ctx *ctx, double dt);
+
+/* Solve B W = R (or the untransformed system for K) to
+ * ||R - B W||_2 <= rtol ||R||_2 by restarted right-preconditioned FGMRES
+ * from W = 0.  Refactors if dt differs from the factored dt.
+ *   R, W      s*T*m stage-major, in mem_space; W may not alias R.
+ *   iters     total inner iterations (may be NULL).
+ *   relres    final true relative residual ||R - B W|| / ||R|| (may be NULL).
+ * Returns IRK_OK, IRK_NOT_CONVERGED (W holds the last iterate) or an error. */
+IRK_API int irk_solve(irk_ctx *ctx, const double *R, double dt, double rtol, double *W, int mem_space,
+              int *iters, double *relres);
+
+/* Y = B X for the context's formulation and dt (the operator product of
+ * Sec. 4.1 alone; Table 2's transformed / untransformed matrix-vector
+ * product).  X, Y stage-major s*T*m in mem_space. */
+IRK_API int irk_apply_operator(irk_ctx *ctx, const double *X, double *Y, double dt, int mem_space);
+
+/* Z = P^{-1} V with the current factors (Sec. 4.2-4.3); IRK_ERR_STATE if
+ * irk_factor has not run.  V, Z stage-major s*T*m in mem_space. */
+IRK_API int irk_apply_precond(irk_ctx *ctx, const double *V, double *Z, int mem_space);
+
+/* Counters of the last irk_factor / irk_solve (host values). */
+typedef struct {
+    int iters, cycles, levels_lower, levels_upper;
+    double relres, factor_ms, solve_ms;
+    long long kernel_launches;  /* kernels launched by the last factor + solve */
+    /* with irk_options.timing = 1 (else 0): device time of each phase of the
+     * last irk_solve, summed over its calls, from CUDA events on the stream */
+    double matvec_ms, precond_ms, ortho_ms;
+    int n_matvec, n_precond, n_ortho;
+} irk_stats;
+IRK_API int irk_get_stats(const irk_ctx *ctx, irk_stats *out);
+
+/* Release every resource of the context (NULL is allowed). */
+IRK_API void irk_destroy(irk_ctx *ctx);
+
+/* Static message for a status code. */
+IRK_API const char *irk_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IRK_GB300_H */

@@ -1,0 +1,146 @@
+// df64.cuh -- double-float ("double-word") arithmetic on the FP32 pipe.
+//
+// A value is an unevaluated sum hi + lo of two binary32 numbers with
+// |lo| <= ulp(hi)/2, about 48 significant bits.  GB300 runs binary32 FMA about
+// 60x faster than binary64, so the operator product, Gram-Schmidt and
+// residuals of the Krylov solver use this type when the context selects
+// IRK_KRYLOV_DF64.  The algorithms are the published error-free
+// transformations:
+//   TwoSum        Knuth (TAOCP vol. 2), Moller (1965)
+//   FastTwoSum    Dekker (1971), valid when |a| >= |b| or a == 0
+//   TwoProd       with a fused multiply-add (e.g. Muller et al., Handbook of
+//                 Floating-Point Arithmetic, 2nd ed., Sec. 4.4)
+//   DW + DW       "AccurateDWPlusDW", Joldes, Muller & Popescu, ACM TOMS 44
+//                 (2017), Alg. 6 (relative error <= 3u^2)
+//   DW x DW       "DWTimesDW3", ibid., Alg. 12 (relative error <= 4u^2)
+//   dot products  the compensated scheme Dot2 of Ogita, Rump & Oishi, SISC 26
+//                 (2005), extended with the cross terms of double-word inputs.
+// Conversions to and from binary64 use the FP64 pipe and run only at the
+// library boundary.
+#pragma once
+#include <cuda_runtime.h>
+
+struct __align__(8) df64 {
+    float hi, lo;
+};
+
+__device__ __forceinline__ df64 df_make(float h, float l) {
+    df64 r;
+    r.hi = h;
+    r.lo = l;
+    return r;
+}
+
+__device__ __forceinline__ df64 df_from_double(double x) {
+    float h = __double2float_rn(x);
+    float l = __double2float_rn(x - (double)h);
+    return df_make(h, l);
+}
+
+__device__ __forceinline__ double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ df64 df_add(df64 x, df64 y) {
+    float sh, sl, th, tl, vh, vl;
+    two_sum(x.hi, y.hi, sh, sl);
+    two_sum(x.lo, y.lo, th, tl);
+    float c = __fadd_rn(sl, th);
+    fast_two_sum(sh, c, vh, vl);
+    float w = __fadd_rn(tl, vl);
+    float zh, zl;
+    fast_two_sum(vh, w, zh, zl);
+    return df_make(zh, zl);
+}
+
+__device__ __forceinline__ df64 df_neg(df64 x) { return df_make(-x.hi, -x.lo); }
+
+__device__ __forceinline__ df64 df_sub(df64 x, df64 y) { return df_add(x, df_neg(y)); }
+
+__device__ __forceinline__ df64 df_mul(df64 x, df64 y) {
+    float ch = __fmul_rn(x.hi, y.hi);
+    float cl1 = __fmaf_rn(x.hi, y.hi, -ch);
+    float tl0 = __fmul_rn(x.lo, y.lo);
+    float tl1 = __fmaf_rn(x.hi, y.lo, tl0);
+    float cl2 = __fmaf_rn(x.lo, y.hi, tl1);
+    float cl3 = __fadd_rn(cl1, cl2);
+    float zh, zl;
+    fast_two_sum(ch, cl3, zh, zl);
+    return df_make(zh, zl);
+}
+
+// Dot-product accumulator: the running sum is s + c with c collecting the
+// exact rounding errors of every addition and product (not renormalised per
+// term); df_acc_value renormalises.
+struct df_acc {
+    float s, c;
+};
+
+__device__ __forceinline__ df_acc df_acc_zero() {
+    df_acc a;
+    a.s = 0.f;
+    a.c = 0.f;
+    return a;
+}
+
+// acc += x * y
+__device__ __forceinline__ void df_acc_fma(df_acc &acc, df64 x, df64 y) {
+    float p = __fmul_rn(x.hi, y.hi);
+    float e = __fmaf_rn(x.hi, y.hi, -p);
+    float s, t;
+    two_sum(acc.s, p, s, t);
+    float c = __fmaf_rn(x.hi, y.lo, acc.c);
+    c = __fmaf_rn(x.lo, y.hi, c);
+    acc.s = s;
+    acc.c = __fadd_rn(c, __fadd_rn(t, e));
+}
+
+// acc += x (a double-word value)
+__device__ __forceinline__ void df_acc_add(df_acc &acc, df64 x) {
+    float s, t;
+    two_sum(acc.s, x.hi, s, t);
+    acc.s = s;
+    acc.c = __fadd_rn(acc.c, __fadd_rn(t, x.lo));
+}
+
+__device__ __forceinline__ df64 df_acc_value(df_acc a) {
+    float h, l;
+    fast_two_sum(a.s, a.c, h, l);
+    // fast_two_sum needs |s| >= |c|; when s is tiny against c (cancellation
+    // to below the error term) fall back to the general two_sum.
+    if (fabsf(a.s) < fabsf(a.c)) two_sum(a.s, a.c, h, l);
+    return df_make(h, l);
+}
+
+__device__ __forceinline__ df64 df_sqrt(df64 a) {
+    // one Newton step on the binary32 root (Karp & Markstein style):
+    // r = sqrt(hi); result = r + (a - r*r) / (2 r)
+    if (a.hi <= 0.f) return df_make(0.f, 0.f);
+    float r = sqrtf(a.hi);
+    float p = __fmul_rn(r, r);
+    float pe = __fmaf_rn(r, r, -p);
+    float d = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), pe), a.lo);
+    float corr = __fdiv_rn(d, __fmul_rn(2.f, r));
+    float h, l;
+    fast_two_sum(r, corr, h, l);
+    return df_make(h, l);
+}
+
+__device__ __forceinline__ df64 df_div(df64 a, df64 b) {
+    // q1 = a.hi / b.hi; remainder r = a - q1*b (double-word); q2 = r.hi / b.hi
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    df64 r = df_sub(a, df_mul(b, df_make(q1, 0.f)));
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    float h, l;
+    fast_two_sum(q1, q2, h, l);
+    return df_make(h, l);
+}

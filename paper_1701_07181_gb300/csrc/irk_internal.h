@@ -1,0 +1,131 @@
+// irk_internal.h -- internal declarations shared by the library's translation
+// units (context layout, kernel launchers).  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/irk_gb300.h"
+
+#define IRK_MAX_S 8
+#define IRK_MAX_M 128
+
+// Device-side error word values (set by kernels, read by the host).
+#define IRK_DEV_ERR_SINGULAR 1
+#define IRK_DEV_ERR_NONFINITE 2
+#define IRK_DEV_ERR_TIMEOUT 4
+
+// Element type of every Krylov vector: 8 bytes, either a binary64 or a
+// double-float pair (hi, lo).  Vectors are stored element-interleaved:
+// index (i*s + k)*m + a for element i, stage k, component a.
+typedef unsigned long long vec8;
+
+// Coefficients of one system-block of the assembled preconditioner matrix:
+// value = cm * M[mi] + cj * J[jp] (m x m blocks); ids index tables of
+// coefficients rebuilt for every dt.
+struct AsmEntry {
+    int jp;        // position of the J block, or -1
+    int mi;        // element whose mass block enters, or -1
+    int cm_id;     // index into the mass-coefficient table
+    int cj_id;     // index into the Jacobian-coefficient table
+};
+
+// Assembled block system whose block ILU(0) is the preconditioner.
+struct PcSystem {
+    int kind = IRK_PC_NONE;
+    int nb = 0, b = 0;  // block rows, block size
+    long long nnz = 0;  // stored blocks
+    int element_major = 0;  // 1: one (s m)-block per J block (assembled by its own kernel)
+    // pattern (device): row pointers, columns, diagonal position, vector offset
+    int *d_rp = nullptr, *d_ci = nullptr, *d_diag = nullptr, *d_voff = nullptr;
+    AsmEntry *d_asm = nullptr;
+    int *d_rowof = nullptr;  // element-major kind: block row of each stored block
+    // factor-update lists: for lower entry p, pairs (q, pos): B_q -= L_p B_pos
+    int *d_upd_ptr = nullptr, *d_upd = nullptr;
+    // level schedules (rows grouped by level; host copies of the level bounds)
+    std::vector<int> lo_ptr, up_ptr;
+    int *d_lo_rows = nullptr, *d_up_rows = nullptr;
+    // values, column-major blocks: working precision (double or float)
+    void *d_vals = nullptr, *d_dinv = nullptr;
+    // bf16 copies used by the sweeps when factor_prec == IRK_FACTOR_BF16
+    void *d_vals16 = nullptr, *d_dinv16 = nullptr;
+    // intermediate vector of the sweeps (compute precision, element-interleaved)
+    void *d_y = nullptr;
+    int n_cm = 0, n_cj = 0;  // coefficient-table sizes
+};
+
+struct irk_ctx {
+    int dev = 0;
+    cudaStream_t stream = nullptr;
+    int s = 0, T = 0, m = 0, nnzb = 0;
+    long long n = 0, N = 0;  // n = T m, N = s n
+    double A[IRK_MAX_S * IRK_MAX_S], Ainv[IRK_MAX_S * IRK_MAX_S], shift[IRK_MAX_S];
+    irk_options opt;
+    int df = 0;  // 1: Krylov arithmetic is double-float
+    int fprec = IRK_FACTOR_FP64;
+    std::vector<int> h_rp, h_ci;
+    int *d_rp = nullptr, *d_ci = nullptr;
+    vec8 *d_J = nullptr;  // nnzb blocks, column-major, binary64 or double-float
+    vec8 *d_M = nullptr;  // T blocks, column-major
+    PcSystem pc;
+    bool factored = false;
+    double factored_dt = 0.0;
+    // Krylov workspace
+    vec8 *d_V = nullptr, *d_Z = nullptr, *d_x = nullptr, *d_b = nullptr, *d_r = nullptr;
+    double *d_io = nullptr;  // stage-major binary64 staging for inputs / outputs (2 N)
+    double *d_H = nullptr;   // (restart+1) x restart Hessenberg, binary64
+    double *d_cs = nullptr, *d_sn = nullptr, *d_g = nullptr, *d_yls = nullptr;
+    double *d_scal = nullptr;  // scalars: [0] h / norm results ...
+    double *h_scal = nullptr;  // pinned host mirror of a few scalars
+    void *d_part = nullptr;    // per-CTA partial sums of the reductions
+    unsigned int *d_ticket = nullptr;
+    int *d_err = nullptr;
+    int red_blocks = 0;
+    irk_stats stats;
+    long long launches = 0;
+    // phase timing (irk_options.timing): event pool and (kind, start, end) marks
+    std::vector<cudaEvent_t> tev;
+    std::vector<int> tkind;
+    int tused = 0;
+};
+
+// ---- launchers (k_matvec.cu) ----
+// y = B x (mode 0) or y = rhs - B x (mode 1); form: IRK_TRANSFORMED / UNTRANSFORMED
+int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt, int mode);
+// stage-major binary64 <-> element-interleaved vec8
+int launch_to_internal(irk_ctx *c, const double *src, vec8 *dst);
+int launch_to_external(irk_ctx *c, const vec8 *src, double *dst);
+// J/M (row-major binary64, device) -> internal column-major vec8 blocks
+int launch_convert_blocks(irk_ctx *c, const double *src, vec8 *dst, long long nblocks);
+
+// ---- launchers (k_krylov.cu) ----
+// Scalars live in 32-byte slots of c->d_scal (128 slots): 0 = norm results,
+// 1 = residual estimate, 2 + i = h_{i,j} of the current column, 64 + i = y_i.
+#define IRK_SCAL_SLOTS 128
+#define IRK_SCAL_BYTES 32
+#define IRK_MAX_RESTART 60
+// w <- w - h[hprev_slot] vprev (if vprev), then slot out = <w, v> (self: v = w;
+// take_sqrt: store the square root); H_out (if non-null) receives the value.
+int launch_axpy_dot_slot(irk_ctx *c, vec8 *w, const vec8 *vprev, int hprev_slot, const vec8 *v,
+                         int self, int take_sqrt, int out_slot, double *H_out);
+// w <- w / value(slot)  (0 when the value is 0)
+int launch_scale_slot(irk_ctx *c, vec8 *w, int slot);
+// Givens step for column j; writes the residual estimate to slot 1
+int launch_givens(irk_ctx *c, int j, int restart);
+// back-substitution for y (size jl+1) and x += Z y
+int launch_lsq_update(irk_ctx *c, int jl, int restart);
+// g = (beta, 0, ..., 0) with beta from slot 0
+int launch_cycle_start(irk_ctx *c, int restart);
+int launch_fill_zero(irk_ctx *c, vec8 *v, long long n);
+double *irk_est_ptr(irk_ctx *c);
+double *irk_beta_ptr(irk_ctx *c);
+
+// ---- (k_ilu.cu) ----
+int pc_build_pattern(irk_ctx *c);  // host: pattern, levels, update lists, uploads
+int pc_factor(irk_ctx *c, double dt);
+int pc_apply(irk_ctx *c, const vec8 *v, vec8 *z);
+void pc_free(PcSystem &p);
+
+// ---- helpers (api.cu) ----
+int cuda_status(cudaError_t e);

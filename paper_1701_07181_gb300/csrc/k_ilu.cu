@@ -1,0 +1,628 @@
+// k_ilu.cu -- block ILU(0) preconditioners (Sec. 4.2-4.3): assembly of the
+// system blocks, level-scheduled factorisation and level-scheduled forward /
+// backward block sweeps, all s stages in the same launches.
+//
+// One generic engine serves every preconditioner kind: the host assembles the
+// block pattern of the matrix to factor (Sec. 4.3.2: s stage matrices
+// (A^{-1}_kk + alpha_k) M - dt J side by side; Sec. 4.3.1 / Alg. 3: the whole
+// stage-major system; or the element-major system with (s m)-blocks), and the
+// device factorises it in the textbook row-by-row (IKJ) form of block ILU(0)
+// (Alg. 1 with the i < k < j updates; equal to Alg. 2 / Alg. 3 when no two
+// neighbours of an element are neighbours).  Rows with no dependency between
+// them form a level; each level is one launch, one CTA per block row.
+//
+// Blocks are column-major on the device; the diagonal block of every row is
+// stored as its explicit inverse D^{-1} (computed by Gauss-Jordan elimination
+// with partial pivoting), so the backward sweep is two block products.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "arith.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// factor-storage loads (binary64, binary32 or bfloat16 storage)
+__device__ __forceinline__ double ldfac(const double *p) { return __ldg(p); }
+__device__ __forceinline__ float ldfac(const float *p) { return __ldg(p); }
+__device__ __forceinline__ float ldfac(const __nv_bfloat16 *p) { return __bfloat162float(p[0]); }
+
+template <class C>
+struct CT;  // compute-type helpers
+template <>
+struct CT<double> {
+    template <class AR>
+    static __device__ __forceinline__ double from_vec(typename AR::val v) { return AR::to_double(v); }
+    template <class AR>
+    static __device__ __forceinline__ typename AR::val to_vec(double x) { return AR::from_double(x); }
+    static __device__ __forceinline__ double from_store(vec8 raw, int df) {
+        if (df) {
+            float2 f = *reinterpret_cast<float2 *>(&raw);
+            return (double)f.x + (double)f.y;
+        }
+        return __longlong_as_double((long long)raw);
+    }
+};
+template <>
+struct CT<float> {
+    template <class AR>
+    static __device__ __forceinline__ float from_vec(typename AR::val v) { return AR::to_float(v); }
+    template <class AR>
+    static __device__ __forceinline__ typename AR::val to_vec(float x) { return AR::from_float(x); }
+    static __device__ __forceinline__ float from_store(vec8 raw, int df) {
+        if (df) {
+            float2 f = *reinterpret_cast<float2 *>(&raw);
+            return f.x + f.y;
+        }
+        return (float)__longlong_as_double((long long)raw);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Assembly (stage-major kinds): value = cm[cm_id] * M[mi] + cj[cj_id] * J[jp]
+struct AsmTables {
+    double cm[IRK_MAX_S * IRK_MAX_S];
+    double cj[IRK_MAX_S * IRK_MAX_S];
+};
+
+template <class C>
+__global__ void k_assemble(long long nnz, int m, const AsmEntry *ent, const vec8 *J, const vec8 *M, int df,
+                           AsmTables tab, C *vals) {
+    const long long mm = (long long)m * m;
+    const long long total = nnz * mm;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        long long q = e / mm, r = e - q * mm;
+        AsmEntry a = ent[q];
+        double v = 0.0;
+        if (a.mi >= 0) v += tab.cm[a.cm_id] * (double)CT<C>::from_store(M[(long long)a.mi * mm + r], df);
+        if (a.jp >= 0) v += tab.cj[a.cj_id] * (double)CT<C>::from_store(J[(long long)a.jp * mm + r], df);
+        vals[e] = (C)v;
+    }
+}
+
+// Element-major assembly: one (s m) x (s m) block per J block p, entry
+// ((k,a),(l,c)) at column-major index (l m + c) * sm + (k m + a).
+//   form 0: C_kl M_i[a][c] [diag] - dt [k==l] J_p[a][c]
+//   form 1: [k==l][diag] M_i[a][c] - dt C_kl J_p[a][c]
+template <class C>
+__global__ void k_assemble_elem(long long nnzb, int s, int m, int form, const int *rowof, const int *ci,
+                                const vec8 *J, const vec8 *M, int df, AsmTables tab, double dt, C *vals) {
+    const long long sm = (long long)s * m, blk = sm * sm, mm = (long long)m * m;
+    const long long total = nnzb * blk;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
+        long long p = e / blk, r = e - p * blk;
+        long long colbig = r / sm, rowbig = r - colbig * sm;
+        int l = (int)(colbig / m), c = (int)(colbig - (long long)l * m);
+        int k = (int)(rowbig / m), a = (int)(rowbig - (long long)k * m);
+        int i = rowof[p];
+        bool diag = (ci[p] == i);
+        double Jv = (double)CT<C>::from_store(J[p * mm + (long long)c * m + a], df);
+        double Mv = diag ? (double)CT<C>::from_store(M[(long long)i * mm + (long long)c * m + a], df) : 0.0;
+        double coef = tab.cm[k * s + l];
+        double v = (form == 0) ? coef * Mv - (k == l ? dt * Jv : 0.0) : (k == l ? Mv : 0.0) - dt * coef * Jv;
+        vals[e] = (C)v;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Factorisation of one level: one CTA per block row R of the level.
+//   for lower entries p of row R (increasing column i):
+//       L_p = B_p D_i^{-1};  B_q -= L_p B_pos for the (q, pos) update pairs of p
+//   D_R^{-1} = inverse(B_RR)
+// Shared memory: two b x b buffers of the compute type.
+template <class C>
+__device__ void block_load(C *dst, const C *src, int bb) {
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) dst[e] = src[e];
+}
+
+// dst(b x b, global) = X (smem) * Y (smem), column-major
+template <class C>
+__device__ void block_mul_store(C *dst, const C *X, const C *Y, int b) {
+    const int bb = b * b;
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) {
+        int col = e / b, row = e - col * b;
+        C acc = 0;
+        for (int t = 0; t < b; ++t) acc += X[t * b + row] * Y[col * b + t];
+        dst[e] = acc;
+    }
+}
+
+// dst(global) -= X (smem) * Y (smem)
+template <class C>
+__device__ void block_mul_sub(C *dst, const C *X, const C *Y, int b) {
+    const int bb = b * b;
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) {
+        int col = e / b, row = e - col * b;
+        C acc = 0;
+        for (int t = 0; t < b; ++t) acc += X[t * b + row] * Y[col * b + t];
+        dst[e] -= acc;
+    }
+}
+
+// In-place Gauss-Jordan inverse with partial pivoting: A (smem) -> I, Binv (smem) = A^{-1}.
+template <class C>
+__device__ bool gauss_jordan(C *A, C *Binv, int b, C *fcol) {
+    __shared__ int s_piv;
+    __shared__ int s_bad;
+    const int bb = b * b;
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) {
+        int col = e / b, row = e - col * b;
+        Binv[e] = (row == col) ? C(1) : C(0);
+    }
+    if (threadIdx.x == 0) s_bad = 0;
+    __syncthreads();
+    for (int k = 0; k < b; ++k) {
+        if (threadIdx.x < 32) {
+            C best = -1;
+            int bi = k;
+            for (int r = k + threadIdx.x; r < b; r += 32) {
+                C v = fabs(A[k * b + r]);
+                if (v > best) {
+                    best = v;
+                    bi = r;
+                }
+            }
+            for (int d = 16; d > 0; d >>= 1) {
+                C ob = __shfl_down_sync(0xffffffffu, best, d);
+                int oi = __shfl_down_sync(0xffffffffu, bi, d);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (threadIdx.x == 0) {
+                s_piv = bi;
+                if (!(best > C(0))) s_bad = 1;
+            }
+        }
+        __syncthreads();
+        const int piv = s_piv;
+        if (piv != k) {
+            for (int c = threadIdx.x; c < 2 * b; c += blockDim.x) {
+                C *M = c < b ? A : Binv;
+                int cc = c < b ? c : c - b;
+                C t = M[cc * b + k];
+                M[cc * b + k] = M[cc * b + piv];
+                M[cc * b + piv] = t;
+            }
+        }
+        __syncthreads();
+        C pv = A[k * b + k];
+        C ip = (pv != C(0)) ? C(1) / pv : C(0);
+        for (int r = threadIdx.x; r < b; r += blockDim.x) fcol[r] = A[k * b + r];
+        __syncthreads();
+        for (int c = threadIdx.x; c < 2 * b; c += blockDim.x) {
+            C *M = c < b ? A : Binv;
+            int cc = c < b ? c : c - b;
+            M[cc * b + k] *= ip;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 2 * bb; e += blockDim.x) {
+            int which = e >= bb;
+            int ee = which ? e - bb : e;
+            int col = ee / b, row = ee - col * b;
+            if (row == k) continue;
+            C *M = which ? Binv : A;
+            if (!which && col <= k) {
+                if (col == k) M[ee] = C(0);
+                continue;
+            }
+            M[ee] -= fcol[row] * M[col * b + k];
+        }
+        __syncthreads();
+    }
+    return s_bad == 0;
+}
+
+template <class C>
+__global__ void __launch_bounds__(256) k_factor_level(const int *rows, int b, const int *rp, const int *ci,
+                                                      const int *diag, const int *upd_ptr, const int *upd,
+                                                      C *vals, C *dinv, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *X = reinterpret_cast<C *>(smem_raw);
+    C *Y = X + b * b;
+    C *fcol = Y + b * b;
+    const int R = rows[blockIdx.x];
+    const long long bb = (long long)b * b;
+    for (int p = rp[R]; p < rp[R + 1]; ++p) {
+        const int i = ci[p];
+        if (i >= R) break;
+        // L_p = B_p D_i^{-1}
+        block_load(X, vals + (long long)p * bb, (int)bb);
+        block_load(Y, dinv + (long long)i * bb, (int)bb);
+        __syncthreads();
+        block_mul_store(vals + (long long)p * bb, X, Y, b);
+        __syncthreads();
+        block_load(X, vals + (long long)p * bb, (int)bb);  // X = L_p
+        __syncthreads();
+        for (int u = upd_ptr[p]; u < upd_ptr[p + 1]; ++u) {
+            const int q = upd[2 * u], pos = upd[2 * u + 1];
+            block_load(Y, vals + (long long)pos * bb, (int)bb);
+            __syncthreads();
+            block_mul_sub(vals + (long long)q * bb, X, Y, b);
+            __syncthreads();
+        }
+    }
+    block_load(X, vals + (long long)diag[R] * bb, (int)bb);
+    __syncthreads();
+    bool ok = gauss_jordan(X, Y, b, fcol);
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) dinv[(long long)R * bb + e] = Y[e];
+    if (!ok && threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_SINGULAR);
+}
+
+template <class C>
+__global__ void k_to_bf16(long long n, const C *src, __nv_bfloat16 *dst) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
+        dst[e] = __float2bfloat16_rn((float)src[e]);
+}
+
+// ---------------------------------------------------------------------------
+// Sweeps.  A group of b threads owns one block row; thread a owns row a.
+//   forward (level of the lower DAG):  y_R = v_R - sum_{p lower} L_p y_col
+//   backward (level of the upper DAG): z_R = D_R^{-1} (y_R - sum_{p upper} U_p z_col)
+// y and z share one compute-precision buffer (a row's y is replaced by its z).
+template <class AR, class C, class F>
+__global__ void __launch_bounds__(256) k_sweep_fwd(const int *rows, int nrows, int b, const int *rp,
+                                                   const int *ci, const int *voff, const F *vals,
+                                                   const vec8 *v, C *y) {
+    const int groups = blockDim.x / b;
+    const int g = threadIdx.x / b, a = threadIdx.x - g * b;
+    const int idx = blockIdx.x * groups + g;
+    if (g >= groups || idx >= nrows) return;
+    const int R = rows[idx];
+    const long long bb = (long long)b * b;
+    C acc = CT<C>::template from_vec<AR>(AR::ld(v + voff[R] + a));
+    for (int p = rp[R]; p < rp[R + 1]; ++p) {
+        const int col = ci[p];
+        if (col >= R) break;
+        const F *L = vals + (long long)p * bb + a;
+        const C *yc = y + voff[col];
+#pragma unroll 4
+        for (int c = 0; c < b; ++c) acc -= (C)ldfac(L + (long long)c * b) * yc[c];
+    }
+    y[voff[R] + a] = acc;
+}
+
+template <class AR, class C, class F>
+__global__ void __launch_bounds__(256) k_sweep_bwd(const int *rows, int nrows, int b, const int *rp,
+                                                   const int *ci, const int *voff, const F *vals,
+                                                   const F *dinv, C *y, vec8 *z) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *t = reinterpret_cast<C *>(smem_raw);
+    const int groups = blockDim.x / b;
+    const int g = threadIdx.x / b, a = threadIdx.x - g * b;
+    const int idx = blockIdx.x * groups + g;
+    const bool active = (g < groups) && (idx < nrows);
+    const long long bb = (long long)b * b;
+    int R = 0;
+    if (active) {
+        R = rows[idx];
+        C acc = y[voff[R] + a];
+        for (int p = rp[R + 1] - 1; p >= rp[R]; --p) {
+            const int col = ci[p];
+            if (col <= R) break;
+            const F *U = vals + (long long)p * bb + a;
+            const C *zc = y + voff[col];
+#pragma unroll 4
+            for (int c = 0; c < b; ++c) acc -= (C)ldfac(U + (long long)c * b) * zc[c];
+        }
+        t[g * b + a] = acc;
+    }
+    __syncthreads();
+    if (!active) return;
+    const F *D = dinv + (long long)R * bb + a;
+    const C *tg = t + g * b;
+    C acc = 0;
+#pragma unroll 4
+    for (int c = 0; c < b; ++c) acc += (C)ldfac(D + (long long)c * b) * tg[c];
+    y[voff[R] + a] = acc;
+    AR::st(z + voff[R] + a, CT<C>::template to_vec<AR>(acc));
+}
+
+int grid_cap(long long n) {
+    long long g = (n + 255) / 256;
+    if (g > 152LL * 16) g = 152LL * 16;
+    return (int)std::max(1LL, g);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side construction of the pattern, levels and update lists.
+struct HostPattern {
+    int nb = 0, b = 0;
+    std::vector<int> rp, ci, diag, voff, rowof;
+    std::vector<AsmEntry> asmv;
+    std::vector<int> upd_ptr, upd;
+    std::vector<int> lo_rows, lo_ptr, up_rows, up_ptr;
+};
+
+void levels_lower(const HostPattern &h, std::vector<int> &rows, std::vector<int> &ptr) {
+    std::vector<int> lev(h.nb, 0);
+    int maxl = 0;
+    for (int R = 0; R < h.nb; ++R) {
+        int l = 0;
+        for (int p = h.rp[R]; p < h.rp[R + 1]; ++p)
+            if (h.ci[p] < R) l = std::max(l, lev[h.ci[p]] + 1);
+        lev[R] = l;
+        maxl = std::max(maxl, l);
+    }
+    ptr.assign(maxl + 2, 0);
+    for (int R = 0; R < h.nb; ++R) ptr[lev[R] + 1]++;
+    for (int l = 0; l <= maxl; ++l) ptr[l + 1] += ptr[l];
+    rows.assign(h.nb, 0);
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int R = 0; R < h.nb; ++R) rows[fill[lev[R]]++] = R;
+}
+
+void levels_upper(const HostPattern &h, std::vector<int> &rows, std::vector<int> &ptr) {
+    std::vector<int> lev(h.nb, 0);
+    int maxl = 0;
+    for (int R = h.nb - 1; R >= 0; --R) {
+        int l = 0;
+        for (int p = h.rp[R]; p < h.rp[R + 1]; ++p)
+            if (h.ci[p] > R) l = std::max(l, lev[h.ci[p]] + 1);
+        lev[R] = l;
+        maxl = std::max(maxl, l);
+    }
+    ptr.assign(maxl + 2, 0);
+    for (int R = 0; R < h.nb; ++R) ptr[lev[R] + 1]++;
+    for (int l = 0; l <= maxl; ++l) ptr[l + 1] += ptr[l];
+    rows.assign(h.nb, 0);
+    std::vector<int> fill(ptr.begin(), ptr.end() - 1);
+    for (int R = h.nb - 1; R >= 0; --R) rows[fill[lev[R]]++] = R;
+}
+
+int find_in_row(const HostPattern &h, int row, int col) {
+    const int *b = h.ci.data() + h.rp[row], *e = h.ci.data() + h.rp[row + 1];
+    const int *f = std::lower_bound(b, e, col);
+    return (f != e && *f == col) ? (int)(f - h.ci.data()) : -1;
+}
+
+void build_updates(HostPattern &h) {
+    h.upd_ptr.assign(h.ci.size() + 1, 0);
+    h.upd.clear();
+    for (int R = 0; R < h.nb; ++R)
+        for (int p = h.rp[R]; p < h.rp[R + 1]; ++p) {
+            h.upd_ptr[p] = (int)(h.upd.size() / 2);
+            const int i = h.ci[p];
+            if (i < R)
+                for (int q = p + 1; q < h.rp[R + 1]; ++q) {
+                    int pos = find_in_row(h, i, h.ci[q]);
+                    if (pos >= 0) {
+                        h.upd.push_back(q);
+                        h.upd.push_back(pos);
+                    }
+                }
+        }
+    h.upd_ptr[h.ci.size()] = (int)(h.upd.size() / 2);
+}
+
+template <class Tv>
+int upload(Tv **dst, const std::vector<Tv> &src) {
+    size_t bytes = std::max<size_t>(1, src.size()) * sizeof(Tv);
+    if (cudaMalloc((void **)dst, bytes) != cudaSuccess) return IRK_ERR_NOMEM;
+    if (!src.empty() && cudaMemcpy(*dst, src.data(), src.size() * sizeof(Tv), cudaMemcpyHostToDevice) != cudaSuccess)
+        return IRK_ERR_CUDA;
+    return IRK_OK;
+}
+
+size_t csize(int fprec) { return fprec == IRK_FACTOR_FP64 ? 8 : 4; }
+
+}  // namespace
+
+// Build the block pattern of the matrix to factor for the context's
+// preconditioner kind (see the file comment), its level schedules and the
+// update lists of the IKJ factorisation, and allocate the factor storage.
+int pc_build_pattern(irk_ctx *c) {
+    PcSystem &P = c->pc;
+    P.kind = c->opt.precond;
+    if (P.kind == IRK_PC_NONE) return IRK_OK;
+    const int s = c->s, T = c->T, m = c->m;
+    const bool transformed = c->opt.formulation == IRK_TRANSFORMED;
+    const std::vector<int> &rp = c->h_rp, &ci = c->h_ci;
+    HostPattern h;
+    if (P.kind == IRK_PC_UNCOUPLED || P.kind == IRK_PC_COUPLED) {
+        if (P.kind == IRK_PC_UNCOUPLED && !transformed) return IRK_ERR_INVALID;
+        h.nb = s * T;
+        h.b = m;
+        h.rp.push_back(0);
+        for (int k = 0; k < s; ++k)
+            for (int i = 0; i < T; ++i) {
+                auto mass = [&](int l) {  // block (k,i)-(l,i), mass coupling
+                    h.ci.push_back(l * T + i);
+                    h.asmv.push_back(AsmEntry{-1, i, k * s + l, 0});
+                };
+                if (P.kind == IRK_PC_COUPLED && transformed)
+                    for (int l = 0; l < k; ++l) mass(l);
+                int lfirst = (P.kind == IRK_PC_COUPLED && !transformed) ? 0 : k;
+                int llast = (P.kind == IRK_PC_COUPLED && !transformed) ? s - 1 : k;
+                for (int l = lfirst; l <= llast; ++l)
+                    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+                        int j = ci[p];
+                        h.ci.push_back(l * T + j);
+                        if (transformed)  // d_k M - dt J  (uncoupled: d_k = A^{-1}_kk + alpha_k)
+                            h.asmv.push_back(AsmEntry{p, j == i ? i : -1, k * s + k, 0});
+                        else  // [k==l][i==j] M - dt a_kl J
+                            h.asmv.push_back(AsmEntry{p, (j == i && l == k) ? i : -1, 0, k * s + l});
+                    }
+                if (P.kind == IRK_PC_COUPLED && transformed)
+                    for (int l = k + 1; l < s; ++l) mass(l);
+                h.rp.push_back((int)h.ci.size());
+            }
+        for (int R = 0; R < h.nb; ++R) {
+            int k = R / T, i = R - k * T;
+            h.voff.push_back((i * s + k) * m);
+        }
+    } else if (P.kind == IRK_PC_ELEMENT) {
+        h.nb = T;
+        h.b = s * m;
+        h.rp = rp;
+        h.ci = ci;
+        for (int i = 0; i < T; ++i) {
+            h.voff.push_back(i * s * m);
+            for (int p = rp[i]; p < rp[i + 1]; ++p) h.rowof.push_back(i);
+        }
+        P.element_major = 1;
+    } else {
+        return IRK_ERR_INVALID;
+    }
+    const size_t cs = csize(c->fprec);
+    if ((size_t)h.b * h.b * cs * 2 + h.b * cs + 64 > 227 * 1024) return IRK_ERR_INVALID;
+    for (int R = 0; R < h.nb; ++R) {
+        int d = find_in_row(h, R, R);
+        if (d < 0) return IRK_ERR_INVALID;
+        h.diag.push_back(d);
+    }
+    build_updates(h);
+    levels_lower(h, h.lo_rows, h.lo_ptr);
+    levels_upper(h, h.up_rows, h.up_ptr);
+    P.nb = h.nb;
+    P.b = h.b;
+    P.nnz = (long long)h.ci.size();
+    P.lo_ptr = h.lo_ptr;
+    P.up_ptr = h.up_ptr;
+    int rc;
+    if ((rc = upload(&P.d_rp, h.rp)) || (rc = upload(&P.d_ci, h.ci)) || (rc = upload(&P.d_diag, h.diag)) ||
+        (rc = upload(&P.d_voff, h.voff)) || (rc = upload(&P.d_upd_ptr, h.upd_ptr)) ||
+        (rc = upload(&P.d_upd, h.upd)) || (rc = upload(&P.d_lo_rows, h.lo_rows)) ||
+        (rc = upload(&P.d_up_rows, h.up_rows)))
+        return rc;
+    if (P.element_major) {
+        if ((rc = upload(&P.d_rowof, h.rowof))) return rc;
+    } else {
+        if ((rc = upload(&P.d_asm, h.asmv))) return rc;
+    }
+    const long long bb = (long long)P.b * P.b;
+    if (cudaMalloc(&P.d_vals, P.nnz * bb * cs) != cudaSuccess) return IRK_ERR_NOMEM;
+    if (cudaMalloc(&P.d_dinv, (long long)P.nb * bb * cs) != cudaSuccess) return IRK_ERR_NOMEM;
+    if (c->fprec == IRK_FACTOR_BF16) {
+        if (cudaMalloc(&P.d_vals16, P.nnz * bb * 2) != cudaSuccess) return IRK_ERR_NOMEM;
+        if (cudaMalloc(&P.d_dinv16, (long long)P.nb * bb * 2) != cudaSuccess) return IRK_ERR_NOMEM;
+    }
+    if (cudaMalloc(&P.d_y, (size_t)c->N * cs) != cudaSuccess) return IRK_ERR_NOMEM;
+    return IRK_OK;
+}
+
+void pc_free(PcSystem &P) {
+    cudaFree(P.d_rp);
+    cudaFree(P.d_ci);
+    cudaFree(P.d_diag);
+    cudaFree(P.d_voff);
+    cudaFree(P.d_asm);
+    cudaFree(P.d_rowof);
+    cudaFree(P.d_upd_ptr);
+    cudaFree(P.d_upd);
+    cudaFree(P.d_lo_rows);
+    cudaFree(P.d_up_rows);
+    cudaFree(P.d_vals);
+    cudaFree(P.d_dinv);
+    cudaFree(P.d_vals16);
+    cudaFree(P.d_dinv16);
+    cudaFree(P.d_y);
+    P = PcSystem();
+}
+
+template <class C>
+static int factor_impl(irk_ctx *c, double dt) {
+    PcSystem &P = c->pc;
+    const int s = c->s;
+    AsmTables tab;
+    memset(&tab, 0, sizeof(tab));
+    const bool transformed = c->opt.formulation == IRK_TRANSFORMED;
+    if (P.element_major) {
+        const double *C0 = transformed ? c->Ainv : c->A;
+        for (int q = 0; q < s * s; ++q) tab.cm[q] = C0[q];
+        k_assemble_elem<C><<<grid_cap(P.nnz * P.b * P.b), 256, 0, c->stream>>>(
+            P.nnz, s, c->m, transformed ? 0 : 1, P.d_rowof, P.d_ci, c->d_J, c->d_M, c->df, tab, dt, (C *)P.d_vals);
+    } else {
+        if (P.kind == IRK_PC_UNCOUPLED) {
+            for (int k = 0; k < s; ++k) tab.cm[k * s + k] = c->Ainv[k * s + k] + c->shift[k];
+            tab.cj[0] = -dt;
+        } else if (transformed) {
+            for (int q = 0; q < s * s; ++q) tab.cm[q] = c->Ainv[q];
+            tab.cj[0] = -dt;
+        } else {
+            tab.cm[0] = 1.0;
+            for (int q = 0; q < s * s; ++q) tab.cj[q] = -dt * c->A[q];
+        }
+        k_assemble<C><<<grid_cap(P.nnz * c->m * c->m), 256, 0, c->stream>>>(P.nnz, c->m, P.d_asm, c->d_J, c->d_M,
+                                                                           c->df, tab, (C *)P.d_vals);
+    }
+    c->launches++;
+    const int b = P.b;
+    const size_t smem = (size_t)b * b * sizeof(C) * 2 + (size_t)b * sizeof(C);
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k_factor_level<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const int nlev = (int)P.lo_ptr.size() - 1;
+    for (int l = 0; l < nlev; ++l) {
+        int n = P.lo_ptr[l + 1] - P.lo_ptr[l];
+        if (n <= 0) continue;
+        k_factor_level<C><<<n, 256, smem, c->stream>>>(P.d_lo_rows + P.lo_ptr[l], b, P.d_rp, P.d_ci, P.d_diag,
+                                                       P.d_upd_ptr, P.d_upd, (C *)P.d_vals, (C *)P.d_dinv,
+                                                       c->d_err);
+        c->launches++;
+    }
+    if (c->fprec == IRK_FACTOR_BF16) {
+        const long long bb = (long long)b * b;
+        k_to_bf16<C><<<grid_cap(P.nnz * bb), 256, 0, c->stream>>>(P.nnz * bb, (const C *)P.d_vals,
+                                                                  (__nv_bfloat16 *)P.d_vals16);
+        k_to_bf16<C><<<grid_cap(P.nb * bb), 256, 0, c->stream>>>(P.nb * bb, (const C *)P.d_dinv,
+                                                                 (__nv_bfloat16 *)P.d_dinv16);
+        c->launches += 2;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+int pc_factor(irk_ctx *c, double dt) {
+    if (c->pc.kind == IRK_PC_NONE) return IRK_OK;
+    return c->fprec == IRK_FACTOR_FP64 ? factor_impl<double>(c, dt) : factor_impl<float>(c, dt);
+}
+
+template <class AR, class C, class F>
+static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv) {
+    PcSystem &P = c->pc;
+    const int b = P.b;
+    const int groups = std::max(1, 256 / b);
+    const int threads = (groups * b + 31) / 32 * 32;
+    C *y = (C *)P.d_y;
+    const int nlo = (int)P.lo_ptr.size() - 1;
+    for (int l = 0; l < nlo; ++l) {
+        int n = P.lo_ptr[l + 1] - P.lo_ptr[l];
+        if (n <= 0) continue;
+        k_sweep_fwd<AR, C, F><<<(n + groups - 1) / groups, threads, 0, c->stream>>>(
+            P.d_lo_rows + P.lo_ptr[l], n, b, P.d_rp, P.d_ci, P.d_voff, vals, v, y);
+        c->launches++;
+    }
+    const size_t smem = (size_t)groups * b * sizeof(C);
+    const int nup = (int)P.up_ptr.size() - 1;
+    for (int l = 0; l < nup; ++l) {
+        int n = P.up_ptr[l + 1] - P.up_ptr[l];
+        if (n <= 0) continue;
+        k_sweep_bwd<AR, C, F><<<(n + groups - 1) / groups, threads, smem, c->stream>>>(
+            P.d_up_rows + P.up_ptr[l], n, b, P.d_rp, P.d_ci, P.d_voff, vals, dinv, y, z);
+        c->launches++;
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+template <class AR>
+static int apply_ar(irk_ctx *c, const vec8 *v, vec8 *z) {
+    PcSystem &P = c->pc;
+    if (c->fprec == IRK_FACTOR_FP64)
+        return apply_impl<AR, double, double>(c, v, z, (const double *)P.d_vals, (const double *)P.d_dinv);
+    if (c->fprec == IRK_FACTOR_FP32)
+        return apply_impl<AR, float, float>(c, v, z, (const float *)P.d_vals, (const float *)P.d_dinv);
+    return apply_impl<AR, float, __nv_bfloat16>(c, v, z, (const __nv_bfloat16 *)P.d_vals16,
+                                                (const __nv_bfloat16 *)P.d_dinv16);
+}
+
+int pc_apply(irk_ctx *c, const vec8 *v, vec8 *z) {
+    if (c->pc.kind == IRK_PC_NONE) {
+        if (cudaMemcpyAsync(z, v, (size_t)c->N * sizeof(vec8), cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+            return IRK_ERR_CUDA;
+        return IRK_OK;
+    }
+    return c->df ? apply_ar<ArDF>(c, v, z) : apply_ar<ArF64>(c, v, z);
+}

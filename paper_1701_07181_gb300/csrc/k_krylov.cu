@@ -1,0 +1,248 @@
+// k_krylov.cu -- Arnoldi (modified Gram-Schmidt), Givens rotations and the
+// least-squares update of restarted flexible GMRES (Sec. 4: one operator
+// product and one preconditioner application per iteration).
+//
+// Reductions are deterministic: every CTA writes one partial in a fixed
+// order of work, and the last CTA to finish (ticket counter) sums the
+// partials in index order with a fixed tree.  No floating-point atomics, so
+// the same input gives bit-identical results.
+#include "arith.cuh"
+
+namespace {
+
+// Scalars written by the reductions: the binary64 value and its double-float
+// split, so that double-float kernels never touch the FP64 pipe.
+struct Scal {
+    double d;      // value
+    float hi, lo;  // value as a double-float pair
+    double inv;    // 1 / value (0 when value == 0)
+    float ihi, ilo;
+};
+
+template <class AR>
+__device__ __forceinline__ typename AR::val block_reduce(typename AR::val v, typename AR::val *sh) {
+    // warp tree, then the warp results in index order
+    for (int d = 16; d > 0; d >>= 1) v = AR::add(v, AR::shfl_down(v, d));
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    if (w == 0) {
+        v = lane < nw ? sh[lane] : AR::from_float(0.f);
+        for (int d = 16; d > 0; d >>= 1) v = AR::add(v, AR::shfl_down(v, d));
+    }
+    return v;  // valid in thread 0
+}
+
+template <class AR>
+__device__ __forceinline__ typename AR::val scal_val(const Scal *s) {
+    return AR::coef(s->d, s->hi, s->lo);
+}
+
+__device__ __forceinline__ void scal_store_d(Scal *s, double d) {
+    s->d = d;
+    float h = (float)d;
+    s->hi = h;
+    s->lo = (float)(d - (double)h);
+    double inv = d != 0.0 ? 1.0 / d : 0.0;
+    s->inv = inv;
+    h = (float)inv;
+    s->ihi = h;
+    s->ilo = (float)(inv - (double)h);
+}
+
+template <class AR>
+__device__ __forceinline__ void scal_store(Scal *s, typename AR::val v) {
+    scal_store_d(s, AR::to_double(v));
+}
+
+// w <- w - hprev * vprev (if vprev), then out = <w, v> (or ||w|| if take_sqrt
+// and v == w).  out is also copied into H_out (binary64) when non-null.
+template <class AR>
+__global__ void __launch_bounds__(256) k_axpy_dot(long long N, vec8 *w, const vec8 *vprev, const Scal *hprev,
+                                                  const vec8 *v, int self, int take_sqrt, Scal *out,
+                                                  double *H_out, vec8 *part,
+                                                  unsigned int *ticket, int *err) {
+    typedef typename AR::val val;
+    __shared__ val sh[32];
+    __shared__ int s_last;
+    val nh = AR::from_float(0.f);
+    if (vprev) nh = AR::neg(scal_val<AR>(hprev));
+    typename AR::acc acc = AR::zero();
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        val wv = AR::ld(w + e);
+        if (vprev) {
+            wv = AR::add(wv, AR::mul(nh, AR::ld(vprev + e)));
+            AR::st(w + e, wv);
+        }
+        AR::fma(acc, wv, self ? wv : AR::ld(v + e));
+    }
+    val r = block_reduce<AR>(AR::value(acc), sh);
+    if (threadIdx.x == 0) {
+        AR::st(part + blockIdx.x, r);
+        __threadfence();
+        unsigned t = atomicAdd(ticket, 1u);
+        s_last = (t == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    typename AR::acc a2 = AR::zero();
+    for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) AR::add_to(a2, AR::ldcg(part + q));
+    __syncthreads();
+    val tot = block_reduce<AR>(AR::value(a2), sh);
+    if (threadIdx.x == 0) {
+        double d = AR::to_double(tot);
+        if (!isfinite(d)) {
+            atomicOr(err, IRK_DEV_ERR_NONFINITE);
+            d = 0.0;
+        }
+        if (take_sqrt) d = d > 0.0 ? sqrt(d) : 0.0;
+        scal_store_d(out, d);
+        if (H_out) *H_out = d;
+        *ticket = 0u;
+    }
+}
+
+// v_out = w / h, or zero when h == 0 (breakdown).
+template <class AR>
+__global__ void k_scale_inv(long long N, vec8 *w, const Scal *h) {
+    typedef typename AR::val val;
+    const val inv = AR::coef(h->inv, h->ihi, h->ilo);
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x)
+        AR::st(w + e, AR::mul(AR::ld(w + e), inv));
+}
+
+// Givens rotations on column j of H (binary64, one thread).
+__global__ void k_givens(int j, int R, double *H, double *cs, double *sn, double *g, double *est,
+                         int *err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = 0; i < j; ++i) {
+        double a = H[i * R + j], b = H[(i + 1) * R + j];
+        H[i * R + j] = cs[i] * a + sn[i] * b;
+        H[(i + 1) * R + j] = -sn[i] * a + cs[i] * b;
+    }
+    double a = H[j * R + j], b = H[(j + 1) * R + j];
+    double rho = hypot(a, b);
+    if (!isfinite(rho)) {
+        atomicOr(err, IRK_DEV_ERR_NONFINITE);
+        *est = 0.0;
+        return;
+    }
+    double c = rho == 0.0 ? 1.0 : a / rho;
+    double s = rho == 0.0 ? 0.0 : b / rho;
+    cs[j] = c;
+    sn[j] = s;
+    H[j * R + j] = rho;
+    H[(j + 1) * R + j] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    *est = fabs(g[j + 1]);
+}
+
+// y = H(0:jl, 0:jl)^{-1} g(0:jl) (one thread), stored as Scal for the update.
+__global__ void k_backsolve(int jl, int R, const double *H, const double *g, double *y, Scal *ys) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int i = jl; i >= 0; --i) {
+        double acc = g[i];
+        for (int k = i + 1; k <= jl; ++k) acc -= H[i * R + k] * y[k];
+        double d = H[i * R + i];
+        y[i] = d != 0.0 ? acc / d : 0.0;
+        scal_store_d(ys + i, y[i]);
+    }
+}
+
+// x += sum_{i <= jl} y_i Z_i
+template <class AR>
+__global__ void k_update_x(long long N, int jl, vec8 *x, const vec8 *Z, const Scal *ys) {
+    typedef typename AR::val val;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        typename AR::acc acc = AR::zero();
+        AR::add_to(acc, AR::ld(x + e));
+        for (int i = 0; i <= jl; ++i) AR::fma(acc, scal_val<AR>(ys + i), AR::ld(Z + (long long)i * N + e));
+        AR::st(x + e, AR::value(acc));
+    }
+}
+
+__global__ void k_cycle_start(int R, const Scal *beta, double *g) {
+    int t = threadIdx.x;
+    for (int q = t; q <= R; q += blockDim.x) g[q] = (q == 0) ? beta->d : 0.0;
+}
+
+__global__ void k_zero(long long n, vec8 *v) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) v[e] = 0ull;
+}
+
+int grid_stream(long long n) {
+    long long g = (n + 255) / 256;
+    if (g > 152 * 8) g = 152 * 8;
+    if (g < 1) g = 1;
+    return (int)g;
+}
+
+}  // namespace
+
+// Scalar slots in c->d_scal (as Scal):
+//   0: beta / norm results   1: residual estimate (binary64 in .d)
+//   2 + i: h_{i,j} of the current column (i <= restart)
+//   64 + i: y_i of the least-squares solution
+// (slot size 32 bytes; c->d_scal holds 128 slots)
+static Scal *scal(irk_ctx *c, int slot) { return reinterpret_cast<Scal *>(c->d_scal) + slot; }
+
+double *irk_est_ptr(irk_ctx *c) { return &scal(c, 1)->d; }
+double *irk_beta_ptr(irk_ctx *c) { return &scal(c, 0)->d; }
+
+int launch_axpy_dot_slot(irk_ctx *c, vec8 *w, const vec8 *vprev, int hprev_slot, const vec8 *v,
+                         int self, int take_sqrt, int out_slot, double *H_out) {
+    const Scal *hp = vprev ? scal(c, hprev_slot) : nullptr;
+    if (c->df)
+        k_axpy_dot<ArDF><<<c->red_blocks, 256, 0, c->stream>>>(
+            c->N, w, vprev, hp, v, self, take_sqrt, scal(c, out_slot), H_out,
+            reinterpret_cast<vec8 *>(c->d_part), c->d_ticket, c->d_err);
+    else
+        k_axpy_dot<ArF64><<<c->red_blocks, 256, 0, c->stream>>>(
+            c->N, w, vprev, hp, v, self, take_sqrt, scal(c, out_slot), H_out,
+            reinterpret_cast<vec8 *>(c->d_part), c->d_ticket, c->d_err);
+    c->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_scale_slot(irk_ctx *c, vec8 *w, int slot) {
+    int g = grid_stream(c->N);
+    if (c->df)
+        k_scale_inv<ArDF><<<g, 256, 0, c->stream>>>(c->N, w, scal(c, slot));
+    else
+        k_scale_inv<ArF64><<<g, 256, 0, c->stream>>>(c->N, w, scal(c, slot));
+    c->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_givens(irk_ctx *c, int j, int restart) {
+    k_givens<<<1, 32, 0, c->stream>>>(j, restart, c->d_H, c->d_cs, c->d_sn, c->d_g, &scal(c, 1)->d, c->d_err);
+    c->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_lsq_update(irk_ctx *c, int jl, int restart) {
+    k_backsolve<<<1, 32, 0, c->stream>>>(jl, restart, c->d_H, c->d_g, c->d_yls, scal(c, 64));
+    c->launches++;
+    int g = grid_stream(c->N);
+    if (c->df)
+        k_update_x<ArDF><<<g, 256, 0, c->stream>>>(c->N, jl, c->d_x, c->d_Z, scal(c, 64));
+    else
+        k_update_x<ArF64><<<g, 256, 0, c->stream>>>(c->N, jl, c->d_x, c->d_Z, scal(c, 64));
+    c->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_cycle_start(irk_ctx *c, int restart) {
+    k_cycle_start<<<1, 64, 0, c->stream>>>(restart, scal(c, 0), c->d_g);
+    c->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_fill_zero(irk_ctx *c, vec8 *v, long long n) {
+    k_zero<<<grid_stream(n), 256, 0, c->stream>>>(n, v);
+    c->launches++;
+    return cuda_status(cudaGetLastError());
+}

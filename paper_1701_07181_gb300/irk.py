@@ -1,0 +1,218 @@
+"""Thin ctypes binding of ``libirk_gb300.so`` (C ABI in ``include/irk_gb300.h``).
+
+Argument marshalling only: every step of the solve runs in the library's CUDA
+kernels.  Arrays may be numpy arrays (host memory: IRK_HOST) or CUDA torch
+tensors (device memory: IRK_DEVICE); the memory space of a call follows its
+arrays.  There is no CPU fallback: if the library cannot be loaded, every
+call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libirk_gb300.so")
+
+IRK_OK, IRK_NOT_CONVERGED = 0, 1
+IRK_HOST, IRK_DEVICE = 0, 1
+PRECOND = {"none": 0, "uncoupled": 1, "coupled": 2, "element": 3}
+FACTOR_PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
+KRYLOV = {"fp64": 0, "df64": 1}
+FORM = {"transformed": 0, "untransformed": 1}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class IrkError(RuntimeError):
+    def __init__(self, code, what):
+        self.code = code
+        super().__init__("%s failed: %s (%d)" % (what, strerror(code), code))
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("precond", ctypes.c_int),
+                ("factor_prec", ctypes.c_int), ("krylov_arith", ctypes.c_int),
+                ("formulation", ctypes.c_int), ("shift", ctypes.POINTER(ctypes.c_double)),
+                ("stream", ctypes.c_void_p), ("timing", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("levels_lower", ctypes.c_int),
+                ("levels_upper", ctypes.c_int), ("relres", ctypes.c_double),
+                ("factor_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
+                ("kernel_launches", ctypes.c_longlong), ("matvec_ms", ctypes.c_double),
+                ("precond_ms", ctypes.c_double), ("ortho_ms", ctypes.c_double),
+                ("n_matvec", ctypes.c_int), ("n_precond", ctypes.c_int), ("n_ortho", ctypes.c_int)]
+
+
+EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor", "irk_solve",
+           "irk_apply_operator", "irk_apply_precond", "irk_get_stats", "irk_destroy",
+           "irk_strerror"]
+
+
+def load():
+    """Load the library (raises if it is missing: build it with
+    ``python -m paper_1701_07181_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libirk_gb300.so not built; run `python -m paper_1701_07181_gb300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        lib.irk_default_options.argtypes = [ctypes.POINTER(Options)]
+        lib.irk_default_options.restype = None
+        lib.irk_setup.argtypes = [ctypes.POINTER(P), I, P, I, I, P, P, P, P, I, ctypes.POINTER(Options)]
+        lib.irk_update_values.argtypes = [P, P, P, I]
+        lib.irk_factor.argtypes = [P, D]
+        lib.irk_solve.argtypes = [P, P, D, D, P, I, ctypes.POINTER(I), ctypes.POINTER(D)]
+        lib.irk_apply_operator.argtypes = [P, P, P, D, I]
+        lib.irk_apply_precond.argtypes = [P, P, P, I]
+        lib.irk_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+        lib.irk_destroy.argtypes = [P]
+        lib.irk_destroy.restype = None
+        lib.irk_strerror.argtypes = [I]
+        lib.irk_strerror.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def strerror(code: int) -> str:
+    return load().irk_strerror(int(code)).decode()
+
+
+def _is_torch_cuda(a):
+    return hasattr(a, "is_cuda") and a.is_cuda
+
+
+def _ptr(a, dtype):
+    """(pointer, keep-alive, mem_space) of an array argument."""
+    if _is_torch_cuda(a):
+        import torch
+        want = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            a = a.to(want).contiguous()
+        return ctypes.c_void_p(a.data_ptr()), a, IRK_DEVICE
+    if hasattr(a, "detach"):  # CPU torch tensor
+        a = a.detach().numpy()
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return arr.ctypes.data_as(ctypes.c_void_p), arr, IRK_HOST
+
+
+class Solver:
+    """One stage-system context (irk_setup ... irk_destroy)."""
+
+    def __init__(self, s, T, m, row_ptr, col_idx, J, M, A=None, precond="uncoupled",
+                 factor_prec="fp64", krylov="fp64", formulation="transformed", restart=30,
+                 max_iter=3000, shift=None, stream=None, timing=False):
+        lib = load()
+        self._lib = lib
+        self.s, self.T, self.m = int(s), int(T), int(m)
+        self.N = self.s * self.T * self.m
+        opt = Options()
+        lib.irk_default_options(ctypes.byref(opt))
+        opt.restart = int(restart)
+        opt.max_iter = int(max_iter)
+        opt.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
+        opt.factor_prec = FACTOR_PREC[factor_prec] if isinstance(factor_prec, str) else int(factor_prec)
+        opt.krylov_arith = KRYLOV[krylov] if isinstance(krylov, str) else int(krylov)
+        opt.formulation = FORM[formulation] if isinstance(formulation, str) else int(formulation)
+        self._shift = None
+        if shift is not None:
+            self._shift = np.ascontiguousarray(shift, dtype=np.float64)
+            opt.shift = self._shift.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if stream is not None:
+            opt.stream = ctypes.c_void_p(int(stream))
+        opt.timing = 1 if timing else 0
+        self._opt = opt
+        rp, k1, sp1 = _ptr(row_ptr, np.int32)
+        ci, k2, sp2 = _ptr(col_idx, np.int32)
+        Jp, k3, sp3 = _ptr(J, np.float64)
+        Mp, k4, sp4 = _ptr(M, np.float64)
+        if len({sp1, sp2, sp3, sp4}) != 1:
+            raise ValueError("pattern and values must all be host arrays or all CUDA tensors")
+        Ap = None
+        if A is not None:
+            self._A = np.ascontiguousarray(A, dtype=np.float64)
+            Ap = self._A.ctypes.data_as(ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        rc = lib.irk_setup(ctypes.byref(h), self.s, Ap, self.T, self.m, rp, ci, Jp, Mp, sp1,
+                           ctypes.byref(opt))
+        if rc != IRK_OK:
+            raise IrkError(rc, "irk_setup")
+        self._h = h
+
+    def _check(self, rc, what, allow_nc=False):
+        if rc == IRK_OK or (allow_nc and rc == IRK_NOT_CONVERGED):
+            return rc
+        raise IrkError(rc, what)
+
+    def update_values(self, J, M):
+        Jp, k1, sp = _ptr(J, np.float64)
+        Mp, k2, _ = _ptr(M, np.float64)
+        self._check(self._lib.irk_update_values(self._h, Jp, Mp, sp), "irk_update_values")
+
+    def factor(self, dt):
+        self._check(self._lib.irk_factor(self._h, float(dt)), "irk_factor")
+
+    def _out_like(self, a):
+        if _is_torch_cuda(a):
+            import torch
+            return torch.empty(self.N, dtype=torch.float64, device=a.device)
+        return np.empty(self.N, dtype=np.float64)
+
+    def solve(self, R, dt, rtol=1e-8, out=None):
+        """W with B W = R; returns (W, iters, relres, status)."""
+        Rp, keep, sp = _ptr(R, np.float64)
+        W = self._out_like(R) if out is None else out
+        Wp, keepw, spw = _ptr(W, np.float64)
+        if sp != spw:
+            raise ValueError("R and W must be in the same memory space")
+        it = ctypes.c_int(0)
+        rr = ctypes.c_double(0.0)
+        rc = self._lib.irk_solve(self._h, Rp, float(dt), float(rtol), Wp, sp, ctypes.byref(it),
+                                 ctypes.byref(rr))
+        self._check(rc, "irk_solve", allow_nc=True)
+        return W, it.value, rr.value, rc
+
+    def apply_operator(self, X, dt):
+        Xp, keep, sp = _ptr(X, np.float64)
+        Y = self._out_like(X)
+        Yp, keepy, _ = _ptr(Y, np.float64)
+        self._check(self._lib.irk_apply_operator(self._h, Xp, Yp, float(dt), sp), "irk_apply_operator")
+        return Y
+
+    def apply_precond(self, V):
+        Vp, keep, sp = _ptr(V, np.float64)
+        Z = self._out_like(V)
+        Zp, keepz, _ = _ptr(Z, np.float64)
+        self._check(self._lib.irk_apply_precond(self._h, Vp, Zp, sp), "irk_apply_precond")
+        return Z
+
+    def stats(self):
+        st = Stats()
+        self._check(self._lib.irk_get_stats(self._h, ctypes.byref(st)), "irk_get_stats")
+        return {f: getattr(st, f) for f, _ in Stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.irk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
