@@ -1,0 +1,361 @@
+#!/usr/bin/env python
+"""Benchmark: IRK stage-system solves per second at rtol 1e-8.
+
+One step = one full stage-system solve (irk_factor + irk_solve, Sec. 4: the
+preconditioner is rebuilt once per linear solve) for each dt in
+{0.01, 0.1, 1} of the 2D workload T=20000 triangles (periodic 100x100 split
+grid, r=3), p=3 (m=40), Radau IIA s=3, synthetic seeded DG-shaped blocks.
+Solver: FGMRES(30), double-float Krylov arithmetic on the FP32 pipe, shifted
+stage-uncoupled block ILU(0) with FP32 factors, all stages per launch.
+
+Reported beside it: the plain FP64 GPU path (FP64 factors and Krylov, one
+request at a time), per-phase device times with roofline fractions, the
+end-to-end number through host buffers, and the FP64 oracle on the host
+cores (bounded sample, extrapolated).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+For N > 1 launch with torch.distributed.run: every rank solves its own
+independent systems (replicas, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DTS = (0.01, 0.1, 1.0)
+RTOL = 1e-8
+METRIC = "IRK stage-system solves/s at rtol 1e-8"
+UNIT = "solves/s"
+WORKLOAD = ("2D periodic 100x100 split grid, T=20000 triangles, r=3, p=3 (m=40), Radau IIA s=3, "
+            "dt in {0.01,0.1,1}, FGMRES(30) rtol 1e-8, shifted uncoupled block ILU(0)")
+
+
+def algorithmic_bytes(T, m, r, s):
+    """Per-launch algorithmic bytes of the operator product (K1) and of one
+    preconditioner application (K3, FP32 factors, upper blocks shared by the
+    stages), and of one Gram-Schmidt step pair per basis vector."""
+    n = T * m
+    k1 = 8 * (r + 1) * m * m * T + 8 * m * m * T + 16 * s * n
+    k3 = 4 * (s * (r / 2) * m * m * T + s * m * m * T + (r / 2) * m * m * T) + 32 * s * n
+    return k1, k3
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def traffic_record(kernel):
+    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or
+    None when absent or taken on a different source of the kernel."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic_c1.txt")
+    if not os.path.exists(path):
+        return None
+    src = os.path.join(ROOT, "paper_1701_07181_gb300", "csrc")
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 4 and not line.startswith("#") and f[0] == kernel:
+            h = hashlib.sha256(open(os.path.join(src, f[2]), "rb").read()).hexdigest()[:12]
+            return float(f[1]) if h == f[3] else None
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 7:
+                    rows.append(parts)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_sample(P, iters_by_dt):
+    """Oracle (serial C, FP64) on a bounded sample of the workload: the
+    preconditioner build at dt = 0.1 (max_iter 0), and build + 3 FGMRES
+    iterations; solve time per dt = build + iters(dt) * per-iteration time."""
+    import oracle
+    ref = oracle.Problem(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M)
+    t0 = time.perf_counter()
+    ref.solve(P.R, 0.1, rtol=RTOL, max_iter=0)
+    t_build = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    ref.solve(P.R, 0.1, rtol=RTOL, max_iter=3)
+    t_iter = max(0.0, (time.perf_counter() - t0 - t_build) / 3.0)
+    t_solves = [t_build + iters_by_dt[dt] * t_iter for dt in DTS]
+    return len(DTS) / sum(t_solves), t_build, t_iter
+
+
+def oracle_iters():
+    path = os.path.join(ROOT, "tests", "golden", "oracle_iters_c1.txt")
+    out = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if line.strip() and not line.startswith("#"):
+                f = line.split()
+                out[float(f[0])] = int(f[1])
+    return out
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    from paper_1701_07181_gb300 import inputs
+    import oracle
+    P = inputs.config("c1", seed=0)
+    ref = oracle.Problem(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M)
+    iters = oracle_iters()
+    for _ in range(args.warmup):  # untimed: one operator product
+        ref.apply(P.R, 0.1)
+    times = []
+    for k in range(args.steps):
+        dt = DTS[k % len(DTS)]
+        t0 = time.perf_counter()
+        ref.solve(P.R, dt, rtol=RTOL, max_iter=1)
+        t_step = time.perf_counter() - t0
+        times.append((dt, t_step))
+    # each step: preconditioner build + 1 iteration at its dt; per-iteration
+    # time from the operator product + preconditioner share measured in the
+    # sample below
+    t0 = time.perf_counter()
+    ref.solve(P.R, 0.1, rtol=RTOL, max_iter=0)
+    t_build = time.perf_counter() - t0
+    t_iter = max(0.0, statistics.median([t for _, t in times]) - t_build)
+    est = [t_build + iters.get(dt, 20) * t_iter for dt in DTS]
+    value = len(DTS) / sum(est)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(est) / len(DTS), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "solver": "oracle: serial C FP64, uncoupled shifted ILU(0)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "per step: oracle preconditioner build + 1 FGMRES iteration of the "
+                                       "full workload at that step's dt; solve time extrapolated as build + "
+                                       "oracle iteration count (tests/golden/oracle_iters_c1.txt) x "
+                                       "per-iteration time"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--plain-steps", type=int, default=1)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(3, args.warmup)
+
+    import torch
+    from paper_1701_07181_gb300 import inputs, irk
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    P = inputs.config("c1", seed=rank)
+    r = 3
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rp, ci, J, M, R = t(P.row_ptr), t(P.col_idx), t(P.J), t(P.M), t(P.R)
+    W = torch.empty_like(R)
+    S = irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec="fp32", krylov="df64",
+                   timing=True)
+
+    def step(solver, acc=None):
+        for dt in DTS:
+            _, it, rr, rc = solver.solve(R, dt, rtol=RTOL, out=W)
+            if rc != 0 or not rr <= RTOL:
+                raise RuntimeError("solve did not converge: rc=%d relres=%g" % (rc, rr))
+            if acc is not None:
+                st = solver.stats()
+                acc["launches"] += st["kernel_launches"]
+                acc["iters"].append(it)
+                for k in ("matvec_ms", "precond_ms", "ortho_ms", "factor_ms", "solve_ms"):
+                    acc[k] += st[k]
+                for k in ("n_matvec", "n_precond", "n_ortho"):
+                    acc[k] += st[k]
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        v = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        return float(v.item())
+
+    for _ in range(args.warmup):
+        step(S)
+    acc = dict(launches=0, iters=[], matvec_ms=0.0, precond_ms=0.0, ortho_ms=0.0, factor_ms=0.0,
+               solve_ms=0.0, n_matvec=0, n_precond=0, n_ortho=0)
+    clocks = Clocks(local)
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step(S, acc)
+    e1.record()
+    barrier()
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1))
+    solves = world * args.steps * len(DTS)
+    value = solves / (ms / 1000.0)
+
+    # end to end through host buffers (pinned), inputs copied in and the
+    # result copied out on every solve
+    Rh = torch.empty(R.numel(), dtype=torch.float64, pin_memory=True)
+    Rh.copy_(R.cpu())
+    Wh = torch.empty(R.numel(), dtype=torch.float64, pin_memory=True)
+    Rn, Wn = Rh.numpy(), Wh.numpy()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for dt in DTS:
+            S.solve(Rn, dt, rtol=RTOL, out=Wn)
+    barrier()
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
+    e2e = {"value": solves / e2e_s, "unit": UNIT, "h2d_bytes_per_step": len(DTS) * R.numel() * 8,
+           "d2h_bytes_per_step": len(DTS) * R.numel() * 8}
+    st_last = S.stats()
+    S.close()
+
+    # plain FP64 GPU path, one request at a time
+    Sp = irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec="fp64", krylov="fp64")
+    step(Sp)  # warm-up
+    plain_acc = dict(launches=0, iters=[], matvec_ms=0.0, precond_ms=0.0, ortho_ms=0.0, factor_ms=0.0,
+                     solve_ms=0.0, n_matvec=0, n_precond=0, n_ortho=0)
+    barrier()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record()
+    for _ in range(args.plain_steps):
+        step(Sp, plain_acc)
+    p1.record()
+    barrier()
+    plain_ms = max_over_ranks(p0.elapsed_time(p1))
+    plain_value = world * args.plain_steps * len(DTS) / (plain_ms / 1000.0)
+    Sp.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return 0
+
+    k1_bytes, k3_bytes = algorithmic_bytes(P.T, P.m, r, P.s)
+    peak, peak_kind = peaks()
+    mv_avg = acc["matvec_ms"] / max(1, acc["n_matvec"])
+    pc_avg = acc["precond_ms"] / max(1, acc["n_precond"])
+    kernels = {
+        "matvec": {"avg_ms": mv_avg, "launches": acc["n_matvec"], "alg_bytes": k1_bytes,
+                   "achieved_gbs": k1_bytes / (mv_avg * 1e6) if mv_avg > 0 else None},
+        "precond_sweeps": {"avg_ms": pc_avg, "applications": acc["n_precond"], "alg_bytes": k3_bytes,
+                           "achieved_gbs": k3_bytes / (pc_avg * 1e6) if pc_avg > 0 else None},
+        "gram_schmidt_total_ms": acc["ortho_ms"], "factor_total_ms": acc["factor_ms"],
+    }
+    dominant = "precond_sweeps" if acc["precond_ms"] >= acc["matvec_ms"] else "matvec"
+    dk = kernels[dominant]
+    achieved = dk["achieved_gbs"]
+    roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "peak_source": peak_kind + " hbm_gbs",
+                "traffic": traffic_record("k_sweep" if dominant == "precond_sweeps" else "k_matvec")}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "df64 Krylov / f32 factors",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "solves_per_step": len(DTS), "l2": "inputs larger than L2 "
+                       "(J alone 1.0 GB per rank)", "parallelism": "replicas x%d" % world,
+                       "iters_per_solve": acc["iters"][: len(DTS)]},
+            "plain_fp64_gpu": {"value": plain_value, "unit": UNIT, "iters_per_solve": plain_acc["iters"],
+                               "speedup_of_value": value / plain_value},
+            "roofline": roofline, "kernels": kernels, "e2e": e2e,
+            "gpu_launches": acc["launches"], "clocks": clk,
+            "last_solve": {"iters": st_last["iters"], "relres": st_last["relres"]}}
+    if not args.no_cpu_baseline and world == 1:
+        iters = oracle_iters() or {dt: i for dt, i in zip(DTS, plain_acc["iters"])}
+        v, tb, ti = cpu_sample(P, iters)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "oracle (serial C, FP64) preconditioner build (%.1f s) and 3 FGMRES "
+                                          "iterations (%.2f s each) of the full workload at dt=0.1; solves/s "
+                                          "extrapolated with the oracle's iteration counts per dt" % (tb, ti)}
+    print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -97,6 +97,12 @@ enum irk_krylov_arith { IRK_KRYLOV_FP64 = 0, IRK_KRYLOV_DF64 = 1 };
 
 enum irk_formulation { IRK_TRANSFORMED = 0, IRK_UNTRANSFORMED = 1 };
 
+/* Scheduling of the preconditioner's block triangular sweeps.  AUTO: one
+ * persistent launch per application, rows synchronised by per-row flags
+ * (block size <= 128), else LEVELS.  LEVELS: one launch per level of the
+ * block-triangular dependency graph. */
+enum irk_sweep_mode { IRK_SWEEP_AUTO = 0, IRK_SWEEP_LEVELS = 1 };
+
 typedef struct {
     int restart;       /* GMRES restart length (default 30) */
     int max_iter;      /* total inner iterations (default 3000) */
@@ -110,6 +116,7 @@ typedef struct {
     void *stream;      /* cudaStream_t for all work of the context; NULL = default */
     int timing;        /* 1: time each phase of irk_factor / irk_solve with CUDA
                           events on the context's stream (see irk_stats); default 0 */
+    int sweep;         /* enum irk_sweep_mode: how the preconditioner sweeps run */
 } irk_options;
 
 /* Fill *opt with the defaults listed above. */

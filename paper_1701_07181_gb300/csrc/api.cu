@@ -137,12 +137,15 @@ int read_host(void *dst, const void *src, size_t bytes, int mem_space) {
     return IRK_OK;
 }
 
+// Wait for the context's stream and read the device error word (an ordered
+// copy on the same stream into pinned memory: no device-wide synchronisation,
+// so contexts on different streams do not serialise each other).
 int sync_err(irk_ctx *c) {
-    cudaError_t e = cudaStreamSynchronize(c->stream);
+    int *herr = reinterpret_cast<int *>(c->h_scal + 3);
+    cudaError_t e = cudaMemcpyAsync(herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    int err = 0;
-    e = cudaMemcpy(&err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost);
-    if (e != cudaSuccess) return cuda_status(e);
+    const int err = *herr;
     if (err & IRK_DEV_ERR_SINGULAR) return IRK_ERR_SINGULAR;
     if (err & IRK_DEV_ERR_NONFINITE) return IRK_ERR_NONFINITE;
     if (err & IRK_DEV_ERR_TIMEOUT) return IRK_ERR_TIMEOUT;
@@ -248,6 +251,7 @@ void irk_default_options(irk_options *o) {
     o->shift = nullptr;
     o->stream = nullptr;
     o->timing = 0;
+    o->sweep = IRK_SWEEP_AUTO;
 }
 
 const char *irk_strerror(int code) {
@@ -282,7 +286,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
     if (c->opt.restart < 1 || c->opt.restart > IRK_MAX_RESTART || c->opt.max_iter < 0 ||
         c->opt.precond < IRK_PC_NONE || c->opt.precond > IRK_PC_ELEMENT || c->opt.factor_prec < 0 ||
         c->opt.factor_prec > IRK_FACTOR_BF16 || c->opt.krylov_arith < 0 || c->opt.krylov_arith > 1 ||
-        c->opt.formulation < 0 || c->opt.formulation > 1 ||
+        c->opt.formulation < 0 || c->opt.formulation > 1 || c->opt.sweep < 0 || c->opt.sweep > 1 ||
         (c->opt.precond == IRK_PC_UNCOUPLED && c->opt.formulation != IRK_TRANSFORMED)) {
         delete c;
         return IRK_ERR_INVALID;

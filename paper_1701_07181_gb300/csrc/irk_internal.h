@@ -53,6 +53,14 @@ struct PcSystem {
     // intermediate vector of the sweeps (compute precision, element-interleaved)
     void *d_y = nullptr;
     int n_cm = 0, n_cj = 0;  // coefficient-table sizes
+    // persistent sweeps: forward / backward results as self-validating words
+    // {32 value bits, epoch}; the epoch increases with every application
+    int persistent = 0;
+    unsigned long long *d_yll = nullptr, *d_zll = nullptr;
+    int epoch = 0;
+    int coop_blocks = 0;
+    size_t coop_smem = 0;
+    int max_item_blocks = 1;  // most blocks one sweep item reads (incl. D^{-1})
 };
 
 struct irk_ctx {

@@ -22,6 +22,8 @@
 
 #include "arith.cuh"
 
+#define IRK_MAX_GJ 256
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -142,18 +144,26 @@ __device__ void block_mul_sub(C *dst, const C *X, const C *Y, int b) {
     }
 }
 
-// In-place Gauss-Jordan inverse with partial pivoting: A (smem) -> I, Binv (smem) = A^{-1}.
+// In-place Gauss-Jordan inversion with partial (row) pivoting of the b x b
+// column-major matrix A in shared memory; the inverse is written to Out
+// (shared memory).  Step k: pivot row p = argmax_{r >= k} |A(r,k)|, swap rows
+// k and p, scale row k by 1/A(k,k) with A(k,k) replaced by 1, and eliminate
+// column k from every other row with A(r,k) replaced by 0.  The in-place
+// result is (P A)^{-1} for the row permutation P; the inverse of A is that
+// matrix with its columns permuted back (swaps undone in reverse order).
+// Thread layout: thread t updates row r = t % b for columns t / b, t / b + G,
+// ... (G = blockDim / b groups): consecutive threads touch consecutive words
+// of a column (no shared-memory bank conflicts).  Returns false on an exactly
+// zero pivot.
 template <class C>
-__device__ bool gauss_jordan(C *A, C *Binv, int b, C *fcol) {
-    __shared__ int s_piv;
+__device__ bool gauss_jordan(C *A, C *Out, int b, C *fcol) {
+    __shared__ int s_piv[IRK_MAX_GJ];
+    __shared__ C s_pval;
     __shared__ int s_bad;
-    const int bb = b * b;
-    for (int e = threadIdx.x; e < bb; e += blockDim.x) {
-        int col = e / b, row = e - col * b;
-        Binv[e] = (row == col) ? C(1) : C(0);
-    }
+    const int G = blockDim.x / b;
+    const int g = threadIdx.x / b, r = threadIdx.x - g * b;
+    const bool act = g < G;
     if (threadIdx.x == 0) s_bad = 0;
-    __syncthreads();
     for (int k = 0; k < b; ++k) {
         if (threadIdx.x < 32) {
             C best = -1;
@@ -174,46 +184,54 @@ __device__ bool gauss_jordan(C *A, C *Binv, int b, C *fcol) {
                 }
             }
             if (threadIdx.x == 0) {
-                s_piv = bi;
-                if (!(best > C(0))) s_bad = 1;
+                s_piv[k] = bi;
+                s_pval = A[k * b + bi];
+                if (!(best > C(0))) {
+                    s_bad = 1;
+                    s_pval = C(1);
+                }
             }
         }
         __syncthreads();
-        const int piv = s_piv;
-        if (piv != k) {
-            for (int c = threadIdx.x; c < 2 * b; c += blockDim.x) {
-                C *M = c < b ? A : Binv;
-                int cc = c < b ? c : c - b;
-                C t = M[cc * b + k];
-                M[cc * b + k] = M[cc * b + piv];
-                M[cc * b + piv] = t;
+        const int p = s_piv[k];
+        const C pinv = C(1) / s_pval;
+        // swap rows k and p; save column k (post-swap) for the elimination
+        for (int cc = threadIdx.x; cc < b; cc += blockDim.x) {
+            if (p != k) {
+                C t = A[cc * b + k];
+                A[cc * b + k] = A[cc * b + p];
+                A[cc * b + p] = t;
             }
         }
         __syncthreads();
-        C pv = A[k * b + k];
-        C ip = (pv != C(0)) ? C(1) / pv : C(0);
         for (int r = threadIdx.x; r < b; r += blockDim.x) fcol[r] = A[k * b + r];
         __syncthreads();
-        for (int c = threadIdx.x; c < 2 * b; c += blockDim.x) {
-            C *M = c < b ? A : Binv;
-            int cc = c < b ? c : c - b;
-            M[cc * b + k] *= ip;
-        }
+        // scale row k (A(k,k) := 1 first)
+        for (int cc = threadIdx.x; cc < b; cc += blockDim.x) A[cc * b + k] = (cc == k ? C(1) : A[cc * b + k]) * pinv;
         __syncthreads();
-        for (int e = threadIdx.x; e < 2 * bb; e += blockDim.x) {
-            int which = e >= bb;
-            int ee = which ? e - bb : e;
-            int col = ee / b, row = ee - col * b;
-            if (row == k) continue;
-            C *M = which ? Binv : A;
-            if (!which && col <= k) {
-                if (col == k) M[ee] = C(0);
-                continue;
-            }
-            M[ee] -= fcol[row] * M[col * b + k];
+        if (act && r != k) {
+            const C f = fcol[r];
+            for (int cc = g; cc < b; cc += G) A[cc * b + r] = (cc == k ? C(0) : A[cc * b + r]) - f * A[cc * b + k];
         }
         __syncthreads();
     }
+    // undo the row interchanges on the columns: Out(:, j) = A(:, idx[j])
+    __shared__ int s_idx[IRK_MAX_GJ];
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < b; ++j) s_idx[j] = j;
+        for (int k = b - 1; k >= 0; --k) {
+            int q = s_piv[k];
+            int t = s_idx[k];
+            s_idx[k] = s_idx[q];
+            s_idx[q] = t;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        int j = e / b, r = e - j * b;
+        Out[e] = A[s_idx[j] * b + r];
+    }
+    __syncthreads();
     return s_bad == 0;
 }
 
@@ -320,6 +338,302 @@ __global__ void __launch_bounds__(256) k_sweep_bwd(const int *rows, int nrows, i
     for (int c = 0; c < b; ++c) acc += (C)ldfac(D + (long long)c * b) * tg[c];
     y[voff[R] + a] = acc;
     AR::st(z + voff[R] + a, CT<C>::template to_vec<AR>(acc));
+}
+
+// ---------------------------------------------------------------------------
+// Persistent sweeps: one launch applies the whole preconditioner.  The work
+// list is the forward rows in lower-level order followed by the backward rows
+// in upper-level order; warp w takes items w, w + W, w + 2W, ... (W warps in
+// the grid, all resident: cooperative launch).  An item waits until the rows
+// it reads are published (per-row flags set to this application's epoch),
+// computes its row and publishes it.  Every dependency sits earlier in the
+// list, so the lowest unfinished item can always proceed.  Waits are bounded:
+// after IRK_SPIN_LIMIT polls, or as soon as another warp reported a timeout,
+// the warp records IRK_DEV_ERR_TIMEOUT and leaves.
+#define IRK_SPIN_LIMIT (1 << 20)
+#define IRK_PB 4  // values per lane: b <= 128
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Called by all 32 lanes of a warp; the decision is warp-uniform (every lane
+// polls with acquire semantics, the loop exits for all lanes together).
+__device__ __forceinline__ bool wait_epoch(const int *flag, int ep, int *err) {
+    for (int spins = 0;; ++spins) {
+        const int v = ld_acquire(flag);
+        if (__all_sync(0xffffffffu, v == ep)) return true;
+        if (spins > 32) __nanosleep(64);
+        if ((spins & 255) == 255) {
+            const int e = ld_acquire(err);
+            if (__any_sync(0xffffffffu, e != 0)) return false;
+        }
+        if (spins > IRK_SPIN_LIMIT) {
+            if ((threadIdx.x & 31) == 0) atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ float ldcg_c(const float *p) { return __ldcg(p); }
+__device__ __forceinline__ double ldcg_c(const double *p) { return __ldcg(p); }
+
+// Shared-memory staging of factor blocks: cp.async.bulk (TMA bulk copy)
+// completing on an mbarrier; plain loads when the block is not 16-byte
+// aligned / sized.
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_arrive(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+// bounded wait for the given phase parity; false after the limit
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    for (int spins = 0; spins < IRK_SPIN_LIMIT; ++spins) {
+        unsigned ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
+// Stage one block (nbytes, element type F) into a slot: TMA when possible.
+template <class F>
+__device__ __forceinline__ void stage_block(F *slot, const F *src, unsigned nbytes, bool tma,
+                                            unsigned long long *bar) {
+    const int lane = threadIdx.x & 31;
+    if (tma) {
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_arrive(bar, nbytes);
+            tma_load_1d(slot, src, nbytes, bar);
+        }
+    } else {
+        const int n = nbytes / sizeof(F);
+#pragma unroll 8
+        for (int e = lane; e < n; e += 32) slot[e] = src[e];
+        __syncwarp();
+        if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+    }
+}
+
+// Self-validating vector words: a compute-precision value is published as
+// sizeof(C)/4 64-bit words {32 value bits, epoch}.  A reader polls the words
+// themselves (relaxed, L1-bypassing 64-bit loads) until every word carries the
+// current epoch: one round trip per dependency and no flags or fences, since
+// each word is written and read atomically.
+template <class C>
+struct LL;
+template <>
+struct LL<float> {
+    static constexpr int W = 1;
+    static __device__ __forceinline__ void put(unsigned long long *p, float v, int ep) {
+        unsigned long long w = ((unsigned long long)(unsigned)ep << 32) | (unsigned)__float_as_uint(v);
+        asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(w) : "memory");
+    }
+    // returns true and the value when the word carries epoch ep
+    static __device__ __forceinline__ bool get(const unsigned long long *p, int ep, float &v) {
+        unsigned long long w;
+        asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w) : "l"(p) : "memory");
+        v = __uint_as_float((unsigned)(w & 0xffffffffull));
+        return (int)(w >> 32) == ep;
+    }
+};
+template <>
+struct LL<double> {
+    static constexpr int W = 2;
+    static __device__ __forceinline__ void put(unsigned long long *p, double v, int ep) {
+        unsigned long long bits = (unsigned long long)__double_as_longlong(v);
+        unsigned long long e = (unsigned long long)(unsigned)ep << 32;
+        asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p), "l"(e | (bits >> 32)) : "memory");
+        asm volatile("st.relaxed.gpu.global.b64 [%0], %1;" ::"l"(p + 1), "l"(e | (bits & 0xffffffffull)) : "memory");
+    }
+    static __device__ __forceinline__ bool get(const unsigned long long *p, int ep, double &v) {
+        unsigned long long w0, w1;
+        asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w0) : "l"(p) : "memory");
+        asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(w1) : "l"(p + 1) : "memory");
+        v = __longlong_as_double((long long)((w0 << 32) | (w1 & 0xffffffffull)));
+        return (int)(w0 >> 32) == ep && (int)(w1 >> 32) == ep;
+    }
+};
+
+// Poll the b published values of one row (lane holds entries lane + 32u);
+// warp-uniform, bounded, abortable.  Returns false on timeout / abort.
+template <class C>
+__device__ __forceinline__ bool ll_wait_row(const unsigned long long *row, int b, int ep, int *err, C (&out)[IRK_PB]) {
+    const int lane = threadIdx.x & 31;
+    for (int spins = 0;; ++spins) {
+        bool ok = true;
+#pragma unroll
+        for (int u = 0; u < IRK_PB; ++u) {
+            const int cc = lane + 32 * u;
+            if (cc < b) ok &= LL<C>::get(row + (long long)cc * LL<C>::W, ep, out[u]);
+            else out[u] = C(0);
+        }
+        if (__all_sync(0xffffffffu, ok)) return true;
+        if (spins > 64) __nanosleep(32);
+        if ((spins & 255) == 255) {
+            const int e = ld_acquire(err);
+            if (__any_sync(0xffffffffu, e != 0)) return false;
+        }
+        if (spins > IRK_SPIN_LIMIT) {
+            if (lane == 0) atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// Persistent sweep with staged blocks.  Each warp owns NS slots of one block
+// and NS mbarriers.  For an item it issues the copies of its first NS blocks
+// at once (before waiting for any dependency), then consumes block k after
+// the dependency of block k is published and the copy of block k landed,
+// refilling the slot with block k + NS.  y (forward results) and zc
+// (backward results) are published as self-validating words.
+template <class AR, class C, class F>
+__global__ void __launch_bounds__(128) k_sweep_staged(int nb, int b, int NS, const int *lo_rows, const int *up_rows,
+                                                      const int *rp, const int *ci, const int *voff, const F *vals,
+                                                      const F *dinv, const vec8 *v, unsigned long long *yll,
+                                                      unsigned long long *zll, vec8 *z, int ep, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int bb = b * b;
+    const unsigned blk_bytes = (unsigned)(bb * sizeof(F));
+    const size_t slot_stride = ((size_t)blk_bytes + 127) / 128 * 128;
+    const size_t warp_bytes = slot_stride * NS + 128;
+    unsigned char *base = smem_raw + wib * warp_bytes;
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(base + slot_stride * NS);
+    const bool tma = (blk_bytes % 16 == 0);
+    if (lane == 0)
+        for (int s = 0; s < NS; ++s) mbar_init(bars + s);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    __syncwarp();
+    unsigned phase = 0;    // bit s: parity of the next completion of slot s
+    unsigned pending = 0;  // bit s: a copy into slot s is in flight
+    // error exit: wait (bounded) for this warp's copies still in flight
+    auto drain = [&]() {
+        for (int s = 0; s < NS; ++s)
+            if ((pending >> s) & 1u) mbar_wait(bars + s, (phase >> s) & 1u);
+    };
+    const int W = (gridDim.x * blockDim.x) >> 5;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const unsigned FULL = 0xffffffffu;
+    constexpr int LW = LL<C>::W;
+    for (int q = gw; q < 2 * nb; q += W) {
+        const bool fwd = q < nb;
+        const int R = fwd ? lo_rows[q] : up_rows[q - nb];
+        const int vo = voff[R];
+        int pbeg, pend, nblk;
+        if (fwd) {
+            pbeg = rp[R];
+            pend = pbeg;
+            while (pend < rp[R + 1] && ci[pend] < R) ++pend;
+            nblk = pend - pbeg;
+        } else {
+            pend = rp[R + 1];
+            pbeg = pend;
+            while (pbeg > rp[R] && ci[pbeg - 1] > R) --pbeg;
+            nblk = pend - pbeg + 1;
+        }
+        auto block_ptr = [&](int kk) -> const F * {
+            if (fwd) return vals + (long long)(pbeg + kk) * bb;
+            if (kk < pend - pbeg) return vals + (long long)(pend - 1 - kk) * bb;
+            return dinv + (long long)R * bb;
+        };
+        for (int kk = 0; kk < nblk && kk < NS; ++kk) {
+            stage_block<F>(reinterpret_cast<F *>(base + slot_stride * kk), block_ptr(kk), blk_bytes, tma, bars + kk);
+            pending |= 1u << kk;
+        }
+        C acc[IRK_PB];
+        if (fwd) {
+#pragma unroll
+            for (int u = 0; u < IRK_PB; ++u) {
+                int a = lane + 32 * u;
+                acc[u] = (a < b) ? CT<C>::template from_vec<AR>(AR::ld(v + vo + a)) : C(0);
+            }
+        } else if (!ll_wait_row<C>(yll + (long long)vo * LW, b, ep, err, acc)) {
+            drain();
+            return;
+        }
+        const int ndep = fwd ? nblk : nblk - 1;
+        for (int kk = 0; kk < nblk; ++kk) {
+            const int s = kk % NS;
+            const bool is_dinv = !fwd && kk == ndep;
+            C dep[IRK_PB];
+            if (!is_dinv) {
+                const int col = fwd ? ci[pbeg + kk] : ci[pend - 1 - kk];
+                if (!ll_wait_row<C>((fwd ? yll : zll) + (long long)voff[col] * LW, b, ep, err, dep)) {
+                    drain();
+                    return;
+                }
+            } else {
+                // z_R = D^{-1} t with t = y_R - sum U z (held in acc)
+#pragma unroll
+                for (int u = 0; u < IRK_PB; ++u) {
+                    dep[u] = acc[u];
+                    acc[u] = C(0);
+                }
+            }
+            if (!mbar_wait(bars + s, (phase >> s) & 1u)) {
+                if (lane == 0) atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+                drain();
+                return;
+            }
+            phase ^= (1u << s);
+            pending &= ~(1u << s);
+            const F *blk = reinterpret_cast<const F *>(base + slot_stride * s);
+            const C sign = is_dinv ? C(1) : C(-1);
+#pragma unroll
+            for (int uc = 0; uc < IRK_PB; ++uc) {
+                if (32 * uc >= b) break;
+                const int cmax = min(32, b - 32 * uc);
+                for (int l = 0; l < cmax; ++l) {
+                    const C dv = sign * __shfl_sync(FULL, dep[uc], l);
+                    const F *col = blk + (32 * uc + l) * b;
+#pragma unroll
+                    for (int u = 0; u < IRK_PB; ++u) {
+                        int a = lane + 32 * u;
+                        if (a < b) acc[u] += (C)col[a] * dv;
+                    }
+                }
+            }
+            __syncwarp();
+            if (kk + NS < nblk) {
+                stage_block<F>(reinterpret_cast<F *>(base + slot_stride * s), block_ptr(kk + NS), blk_bytes, tma,
+                               bars + s);
+                pending |= 1u << s;
+            }
+        }
+        unsigned long long *dst = (fwd ? yll : zll) + (long long)vo * LW;
+#pragma unroll
+        for (int u = 0; u < IRK_PB; ++u) {
+            int a = lane + 32 * u;
+            if (a < b) {
+                LL<C>::put(dst + (long long)a * LW, acc[u], ep);
+                if (!fwd) AR::st(z + vo + a, CT<C>::template to_vec<AR>(acc[u]));
+            }
+        }
+    }
 }
 
 int grid_cap(long long n) {
@@ -476,6 +790,15 @@ int pc_build_pattern(irk_ctx *c) {
         h.diag.push_back(d);
     }
     build_updates(h);
+    P.max_item_blocks = 1;
+    for (int R = 0; R < h.nb; ++R) {
+        int lower = 0, upper = 0;
+        for (int p = h.rp[R]; p < h.rp[R + 1]; ++p) {
+            if (h.ci[p] < R) ++lower;
+            if (h.ci[p] > R) ++upper;
+        }
+        P.max_item_blocks = std::max(P.max_item_blocks, std::max(lower, upper + 1));
+    }
     levels_lower(h, h.lo_rows, h.lo_ptr);
     levels_upper(h, h.up_rows, h.up_ptr);
     P.nb = h.nb;
@@ -502,6 +825,16 @@ int pc_build_pattern(irk_ctx *c) {
         if (cudaMalloc(&P.d_dinv16, (long long)P.nb * bb * 2) != cudaSuccess) return IRK_ERR_NOMEM;
     }
     if (cudaMalloc(&P.d_y, (size_t)c->N * cs) != cudaSuccess) return IRK_ERR_NOMEM;
+    P.persistent = (P.b <= 128) && c->opt.sweep != IRK_SWEEP_LEVELS;
+    if (P.persistent) {
+        // self-validating words: cs/4 words of 8 bytes per value, epoch 0 = never written
+        const size_t words = (size_t)c->N * (cs / 4);
+        if (cudaMalloc(&P.d_yll, words * 8) != cudaSuccess) return IRK_ERR_NOMEM;
+        if (cudaMalloc(&P.d_zll, words * 8) != cudaSuccess) return IRK_ERR_NOMEM;
+        cudaMemset(P.d_yll, 0, words * 8);
+        cudaMemset(P.d_zll, 0, words * 8);
+        P.epoch = 0;
+    }
     return IRK_OK;
 }
 
@@ -521,6 +854,8 @@ void pc_free(PcSystem &P) {
     cudaFree(P.d_vals16);
     cudaFree(P.d_dinv16);
     cudaFree(P.d_y);
+    cudaFree(P.d_yll);
+    cudaFree(P.d_zll);
     P = PcSystem();
 }
 
@@ -581,9 +916,41 @@ int pc_factor(irk_ctx *c, double dt) {
 }
 
 template <class AR, class C, class F>
+static int apply_persistent(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv) {
+    PcSystem &P = c->pc;
+    auto kern = k_sweep_staged<AR, C, F>;
+    const int threads = 128, warps = threads / 32;
+    const size_t blk_bytes = (size_t)P.b * P.b * sizeof(F);
+    const size_t slot_stride = (blk_bytes + 127) / 128 * 128;
+    // slots per warp: the longest item, within about 48 KB per warp
+    int NS = std::max(1, std::min(std::min(P.max_item_blocks, 16), (int)((48 * 1024) / slot_stride)));
+    const size_t warp_bytes = slot_stride * NS + 128;
+    const size_t smem = warp_bytes * warps;
+    if (smem > 227 * 1024) return IRK_ERR_INVALID;
+    if (P.coop_blocks == 0 || P.coop_smem != smem) {
+        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        int per_sm = 0, sms = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
+        P.coop_blocks = per_sm * sms;
+        P.coop_smem = smem;
+        if (P.coop_blocks <= 0) return IRK_ERR_CUDA;
+    }
+    int nb = P.nb, b = P.b, ep = ++P.epoch;
+    const int *lo = P.d_lo_rows, *up = P.d_up_rows, *rp = P.d_rp, *ci = P.d_ci, *vo = P.d_voff;
+    unsigned long long *yll = P.d_yll, *zll = P.d_zll;
+    int *err = c->d_err;
+    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &vo, &vals, &dinv, &v, &yll, &zll, &z, &ep, &err};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, P.coop_blocks, threads, args, smem, c->stream);
+    c->launches++;
+    return cuda_status(e);
+}
+
+template <class AR, class C, class F>
 static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv) {
     PcSystem &P = c->pc;
     const int b = P.b;
+    if (P.persistent) return apply_persistent<AR, C, F>(c, v, z, vals, dinv);
     const int groups = std::max(1, 256 / b);
     const int threads = (groups * b + 31) / 32 * 32;
     C *y = (C *)P.d_y;

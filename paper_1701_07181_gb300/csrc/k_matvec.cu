@@ -29,7 +29,28 @@ struct MatvecParams {
     KCoef mdt;                       // -dt
 };
 
-template <class AR, int S>
+// dst[l] += sum_c B[c][a] x[l][c] for one column-major block (thread's row a
+// pre-applied to B).  Chunks of CH columns: all loads of a chunk are issued
+// before its arithmetic, so every thread keeps CH block loads in flight.
+template <class AR, int S, int CH>
+__device__ __forceinline__ void accum_block(typename AR::acc (&dst)[S], const vec8 *B, const vec8 *x, int m) {
+    typedef typename AR::val val;
+    for (int c0 = 0; c0 < m; c0 += CH) {
+        val bv[CH], xv[S][CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) bv[u] = (c0 + u < m) ? AR::ld(B + (long long)(c0 + u) * m) : AR::from_float(0.f);
+#pragma unroll
+        for (int l = 0; l < S; ++l)
+#pragma unroll
+            for (int u = 0; u < CH; ++u) xv[l][u] = (c0 + u < m) ? AR::ld(x + l * m + c0 + u) : AR::from_float(0.f);
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+#pragma unroll
+            for (int l = 0; l < S; ++l) AR::fma(dst[l], bv[u], xv[l][u]);
+    }
+}
+
+template <class AR, int S, int CH>
 __global__ void __launch_bounds__(256) k_matvec(MatvecParams P) {
     typedef typename AR::val val;
     typedef typename AR::acc acc;
@@ -48,24 +69,9 @@ __global__ void __launch_bounds__(256) k_matvec(MatvecParams P) {
             z[l] = AR::zero();
         }
         const int p0 = P.rp[i], p1 = P.rp[i + 1];
-        for (int p = p0; p < p1; ++p) {
-            const vec8 *Jb = P.J + (long long)p * mm + a;
-            const vec8 *xj = P.x + (long long)P.ci[p] * sm;
-#pragma unroll 4
-            for (int c = 0; c < m; ++c) {
-                val jv = AR::ld(Jb + (long long)c * m);
-#pragma unroll
-                for (int l = 0; l < S; ++l) AR::fma(t[l], jv, AR::ld(xj + l * m + c));
-            }
-        }
-        const vec8 *Mb = P.M + i * mm + a;
-        const vec8 *xi = P.x + i * sm;
-#pragma unroll 4
-        for (int c = 0; c < m; ++c) {
-            val mv = AR::ld(Mb + (long long)c * m);
-#pragma unroll
-            for (int l = 0; l < S; ++l) AR::fma(z[l], mv, AR::ld(xi + l * m + c));
-        }
+        for (int p = p0; p < p1; ++p)
+            accum_block<AR, S, CH>(t, P.J + (long long)p * mm + a, P.x + (long long)P.ci[p] * sm, m);
+        accum_block<AR, S, CH>(z, P.M + i * mm + a, P.x + i * sm, m);
         val tv[S], zv[S];
 #pragma unroll
         for (int l = 0; l < S; ++l) {
@@ -149,7 +155,11 @@ void run_matvec(const MatvecParams &P, cudaStream_t st) {
     int threads = groups * P.m;
     threads = (threads + 31) / 32 * 32;
     long long g = (P.T + groups - 1) / groups;
-    k_matvec<AR, S><<<(int)g, threads, 0, st>>>(P);
+    // chunk width: 8 columns for up to 3 stages, 4 beyond (register budget)
+    if (S <= 3)
+        k_matvec<AR, S, 8><<<(int)g, threads, 0, st>>>(P);
+    else
+        k_matvec<AR, S, 4><<<(int)g, threads, 0, st>>>(P);
 }
 
 template <class AR>

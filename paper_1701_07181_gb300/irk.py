@@ -38,7 +38,7 @@ class Options(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("precond", ctypes.c_int),
                 ("factor_prec", ctypes.c_int), ("krylov_arith", ctypes.c_int),
                 ("formulation", ctypes.c_int), ("shift", ctypes.POINTER(ctypes.c_double)),
-                ("stream", ctypes.c_void_p), ("timing", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("timing", ctypes.c_int), ("sweep", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -110,7 +110,7 @@ class Solver:
 
     def __init__(self, s, T, m, row_ptr, col_idx, J, M, A=None, precond="uncoupled",
                  factor_prec="fp64", krylov="fp64", formulation="transformed", restart=30,
-                 max_iter=3000, shift=None, stream=None, timing=False):
+                 max_iter=3000, shift=None, stream=None, timing=False, sweep="auto"):
         lib = load()
         self._lib = lib
         self.s, self.T, self.m = int(s), int(T), int(m)
@@ -130,6 +130,7 @@ class Solver:
         if stream is not None:
             opt.stream = ctypes.c_void_p(int(stream))
         opt.timing = 1 if timing else 0
+        opt.sweep = {"auto": 0, "levels": 1}[sweep]
         self._opt = opt
         rp, k1, sp1 = _ptr(row_ptr, np.int32)
         ci, k2, sp2 = _ptr(col_idx, np.int32)
