@@ -67,7 +67,9 @@ enum irk_status {
     IRK_ERR_NONFINITE = -4,/* NaN/Inf in a residual or Krylov quantity */
     IRK_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
     IRK_ERR_CUDA = -6,     /* a CUDA runtime call failed */
-    IRK_ERR_STATE = -7     /* call out of order (e.g. apply before factor) */
+    IRK_ERR_STATE = -7,    /* call out of order (e.g. apply before factor) */
+    IRK_ERR_SCRATCH_LIMIT = -8 /* problem too large for the fixed scratch of
+                                  irk_apply_precond_noalloc */
 };
 
 enum irk_mem_space { IRK_HOST = 0, IRK_DEVICE = 1 };
@@ -164,6 +166,43 @@ IRK_API int irk_apply_operator(irk_ctx *ctx, const double *X, double *Y, double 
 /* Z = P^{-1} V with the current factors (Sec. 4.2-4.3); IRK_ERR_STATE if
  * irk_factor has not run.  V, Z stage-major s*T*m in mem_space. */
 IRK_API int irk_apply_precond(irk_ctx *ctx, const double *V, double *Z, int mem_space);
+
+/* Preconditioner application that allocates nothing.
+ * The paper has no counterpart; this is a convenience of this library.
+ *
+ * Who needs it: callers that cannot allocate device memory at the moment
+ * they apply the preconditioner -- for instance a time-stepping driver whose
+ * GPU memory is entirely held by another allocator's pool (a framework's
+ * caching allocator that has already reserved the device), or a loop with a
+ * rule against allocation after start-up because cudaMalloc synchronises the
+ * device and stalls latency-critical work.  irk_apply_precond uses buffers the
+ * context allocated at irk_setup; this variant instead keeps its working
+ * vectors in one fixed array of IRK_NOALLOC_SCRATCH_BYTES bytes that the
+ * library declares in device memory, so the call itself never calls
+ * cudaMalloc, cudaFree or any allocating routine.
+ *
+ * Computes Z = P^{-1} V exactly like irk_apply_precond (same kernels, same
+ * factors) for a context that irk_factor has prepared.
+ *   V, Z    DEVICE pointers, s*T*m values, stage-major (as irk_solve); Z must
+ *           not alias V.  The caller owns both.
+ *   stream  cudaStream_t to run on (NULL = legacy default stream); the call
+ *           waits for its own work before returning.
+ * Limits and errors:
+ *   - the working set is 16 + 16*w bytes per unknown (w = 1 with FP32/BF16
+ *     factors, 2 with FP64 factors) plus 256 bytes; a larger system returns
+ *     IRK_ERR_SCRATCH_LIMIT (with FP32 factors: up to 2,097,120 unknowns);
+ *   - IRK_ERR_STATE if the context is not factored; IRK_ERR_INVALID if it has
+ *     no preconditioner, uses per-level sweeps (block size > 128 or
+ *     IRK_SWEEP_LEVELS), or belongs to another device than the current one.
+ * Set-up: the first call on a device (with that device current) looks up
+ * the array's device address once; make that first call before any stream
+ * capture.  The array is shared by every call on a device and keeps the last
+ * call's contents (each call clears what it needs cleared), so calls that
+ * overlap on the GPU -- from several threads or streams at once -- race and
+ * must be serialised by the caller.  Every GPU that loads the library holds
+ * the array until the process exits. */
+#define IRK_NOALLOC_SCRATCH_BYTES (64u << 20)
+IRK_API int irk_apply_precond_noalloc(irk_ctx *ctx, const double *V, double *Z, void *stream);
 
 /* Counters of the last irk_factor / irk_solve (host values). */
 typedef struct {

@@ -265,6 +265,7 @@ const char *irk_strerror(int code) {
         case IRK_ERR_TIMEOUT: return "bounded device wait timed out";
         case IRK_ERR_CUDA: return "CUDA runtime error";
         case IRK_ERR_STATE: return "call out of order";
+        case IRK_ERR_SCRATCH_LIMIT: return "system too large for the fixed scratch of irk_apply_precond_noalloc";
         default: return "unknown status";
     }
 }

@@ -18,6 +18,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "arith.cuh"
@@ -992,4 +993,130 @@ int pc_apply(irk_ctx *c, const vec8 *v, vec8 *z) {
         return IRK_OK;
     }
     return c->df ? apply_ar<ArDF>(c, v, z) : apply_ar<ArF64>(c, v, z);
+}
+
+// ---------------------------------------------------------------------------
+// irk_apply_precond_noalloc: the preconditioner application with its working
+// vectors in a fixed device array instead of context-owned buffers, for
+// callers that cannot allocate (see the header).  Layout of the array:
+// [error word | 256 B] [V internal | N vec8] [Z internal | N vec8]
+// [forward words | N*w] [backward words | N*w], each region 256-byte aligned.
+static __device__ __align__(256) unsigned char irk_noalloc_scratch[IRK_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+#define IRK_NOALLOC_MAX_DEVICES 64
+unsigned char *g_noalloc_base[IRK_NOALLOC_MAX_DEVICES];
+std::mutex g_noalloc_mutex;
+
+size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
+
+template <class AR>
+__global__ void k_na_in(long long N, int T, int m, int s, const double *__restrict__ src, vec8 *dst) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        long long a = e % m, r = e / m, k = r % s, i = r / s;
+        AR::st(dst + e, AR::from_double(src[(k * T + i) * m + a]));
+    }
+}
+
+template <class AR>
+__global__ void k_na_out(long long N, int T, int m, int s, const vec8 *__restrict__ src, double *dst) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
+        long long a = e % m, r = e / m, k = r % s, i = r / s;
+        dst[(k * T + i) * m + a] = AR::to_double(AR::ld(src + e));
+    }
+}
+
+template <class AR, class C, class F>
+int na_sweep(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv, unsigned long long *yll,
+             unsigned long long *zll, int *err, cudaStream_t st) {
+    PcSystem &P = c->pc;
+    auto kern = k_sweep_staged<AR, C, F>;
+    const int threads = 128, warps = threads / 32;
+    const size_t blk_bytes = (size_t)P.b * P.b * sizeof(F);
+    const size_t slot_stride = (blk_bytes + 127) / 128 * 128;
+    int NS = std::max(1, std::min(std::min(P.max_item_blocks, 16), (int)((48 * 1024) / slot_stride)));
+    const size_t smem = (slot_stride * NS + 128) * warps;
+    if (smem > 227 * 1024) return IRK_ERR_INVALID;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return IRK_ERR_CUDA;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess || per_sm <= 0)
+        return IRK_ERR_CUDA;
+    int grid = per_sm * sms;
+    int nb = P.nb, b = P.b, ep = 1;
+    const int *lo = P.d_lo_rows, *up = P.d_up_rows, *rp = P.d_rp, *ci = P.d_ci, *vo = P.d_voff;
+    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &vo, &vals, &dinv, &v, &yll, &zll, &z, &ep, &err};
+    return cuda_status(cudaLaunchCooperativeKernel((const void *)kern, grid, threads, args, smem, st));
+}
+
+template <class AR>
+int na_sweep_prec(irk_ctx *c, const vec8 *v, vec8 *z, unsigned long long *yll, unsigned long long *zll, int *err,
+                  cudaStream_t st) {
+    PcSystem &P = c->pc;
+    if (c->fprec == IRK_FACTOR_FP64)
+        return na_sweep<AR, double, double>(c, v, z, (const double *)P.d_vals, (const double *)P.d_dinv, yll, zll,
+                                            err, st);
+    if (c->fprec == IRK_FACTOR_FP32)
+        return na_sweep<AR, float, float>(c, v, z, (const float *)P.d_vals, (const float *)P.d_dinv, yll, zll, err,
+                                          st);
+    return na_sweep<AR, float, __nv_bfloat16>(c, v, z, (const __nv_bfloat16 *)P.d_vals16,
+                                              (const __nv_bfloat16 *)P.d_dinv16, yll, zll, err, st);
+}
+
+}  // namespace
+
+extern "C" int irk_apply_precond_noalloc(irk_ctx *c, const double *V, double *Z, void *stream) {
+    if (!c || !V || !Z || V == Z) return IRK_ERR_INVALID;
+    if (c->pc.kind == IRK_PC_NONE || !c->pc.persistent) return IRK_ERR_INVALID;
+    if (!c->factored) return IRK_ERR_STATE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev != c->dev || dev < 0 || dev >= IRK_NOALLOC_MAX_DEVICES)
+        return IRK_ERR_INVALID;
+    const size_t N = (size_t)c->N;
+    const size_t w = (c->fprec == IRK_FACTOR_FP64) ? 2 : 1;
+    const size_t need = 256 + 2 * na_align(N * 8) + 2 * na_align(N * 8 * w);
+    if (need > IRK_NOALLOC_SCRATCH_BYTES) return IRK_ERR_SCRATCH_LIMIT;
+    unsigned char *base;
+    {
+        std::lock_guard<std::mutex> g(g_noalloc_mutex);
+        if (!g_noalloc_base[dev]) {
+            void *p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, irk_noalloc_scratch);
+            if (e != cudaSuccess || !p) return IRK_ERR_CUDA;
+            g_noalloc_base[dev] = (unsigned char *)p;
+        }
+        base = g_noalloc_base[dev];
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    int *err = reinterpret_cast<int *>(base);
+    vec8 *vin = reinterpret_cast<vec8 *>(base + 256);
+    vec8 *vout = reinterpret_cast<vec8 *>(base + 256 + na_align(N * 8));
+    unsigned long long *yll = reinterpret_cast<unsigned long long *>(base + 256 + 2 * na_align(N * 8));
+    unsigned long long *zll = reinterpret_cast<unsigned long long *>(base + 256 + 2 * na_align(N * 8) + na_align(N * 8 * w));
+    // what must start at zero: the error word and the published words (epoch 0 = unwritten)
+    if (cudaMemsetAsync(err, 0, 256, st) != cudaSuccess ||
+        cudaMemsetAsync(yll, 0, 2 * na_align(N * 8 * w), st) != cudaSuccess)
+        return IRK_ERR_CUDA;
+    const int g = grid_cap((long long)N);
+    int rc;
+    if (c->df) {
+        k_na_in<ArDF><<<g, 256, 0, st>>>((long long)N, c->T, c->m, c->s, V, vin);
+        rc = cuda_status(cudaGetLastError());
+        if (!rc) rc = na_sweep_prec<ArDF>(c, vin, vout, yll, zll, err, st);
+        if (!rc) k_na_out<ArDF><<<g, 256, 0, st>>>((long long)N, c->T, c->m, c->s, vout, Z);
+    } else {
+        k_na_in<ArF64><<<g, 256, 0, st>>>((long long)N, c->T, c->m, c->s, V, vin);
+        rc = cuda_status(cudaGetLastError());
+        if (!rc) rc = na_sweep_prec<ArF64>(c, vin, vout, yll, zll, err, st);
+        if (!rc) k_na_out<ArF64><<<g, 256, 0, st>>>((long long)N, c->T, c->m, c->s, vout, Z);
+    }
+    if (!rc) rc = cuda_status(cudaGetLastError());
+    int herr = 0;
+    if (!rc) rc = cuda_status(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
+    if (!rc && (herr & IRK_DEV_ERR_TIMEOUT)) rc = IRK_ERR_TIMEOUT;
+    return rc;
 }

@@ -52,7 +52,7 @@ class Stats(ctypes.Structure):
 
 EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor", "irk_solve",
            "irk_apply_operator", "irk_apply_precond", "irk_get_stats", "irk_destroy",
-           "irk_strerror"]
+           "irk_strerror", "irk_apply_precond_noalloc"]
 
 
 def load():
@@ -79,6 +79,7 @@ def load():
         lib.irk_destroy.restype = None
         lib.irk_strerror.argtypes = [I]
         lib.irk_strerror.restype = ctypes.c_char_p
+        lib.irk_apply_precond_noalloc.argtypes = [P, P, P, P]
         _lib = lib
         return lib
 
