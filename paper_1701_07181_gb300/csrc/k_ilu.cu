@@ -79,10 +79,10 @@ __global__ void k_assemble(long long nnz, int m, const AsmEntry *ent, const vec8
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
         long long q = e / mm, r = e - q * mm;
         AsmEntry a = ent[q];
-        double v = 0.0;
-        if (a.mi >= 0) v += tab.cm[a.cm_id] * (double)CT<C>::from_store(M[(long long)a.mi * mm + r], df);
-        if (a.jp >= 0) v += tab.cj[a.cj_id] * (double)CT<C>::from_store(J[(long long)a.jp * mm + r], df);
-        vals[e] = (C)v;
+        C v = C(0);
+        if (a.mi >= 0) v += (C)tab.cm[a.cm_id] * CT<C>::from_store(M[(long long)a.mi * mm + r], df);
+        if (a.jp >= 0) v += (C)tab.cj[a.cj_id] * CT<C>::from_store(J[(long long)a.jp * mm + r], df);
+        vals[e] = v;
     }
 }
 
@@ -268,6 +268,203 @@ __global__ void __launch_bounds__(256) k_factor_level(const int *rows, int b, co
     block_load(X, vals + (long long)diag[R] * bb, (int)bb);
     __syncthreads();
     bool ok = gauss_jordan(X, Y, b, fcol);
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) dinv[(long long)R * bb + e] = Y[e];
+    if (!ok && threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_SINGULAR);
+}
+
+// Gauss-Jordan with three barriers per pivot (the fast path of the
+// factorisation).  Same algorithm and result as gauss_jordan above: phase 1
+// finds the pivot; phase 2 performs the row interchange and the scaling of
+// the pivot row together (each thread owns whole columns c != k) and saves
+// the post-interchange pivot column; phase 3 eliminates, writing column k as
+// -f_r / pivot (rows r != k) and 1 / pivot (row k).
+template <class C>
+__device__ bool gauss_jordan3(C *A, C *Out, int b, C *fcol) {
+    __shared__ int s_piv[IRK_MAX_GJ];
+    __shared__ C s_pinv;
+    __shared__ int s_bad;
+    const int G = blockDim.x / b;
+    const int g = threadIdx.x / b, r = threadIdx.x - g * b;
+    const bool act = g < G;
+    if (threadIdx.x == 0) s_bad = 0;
+    for (int k = 0; k < b; ++k) {
+        if (threadIdx.x < 32) {
+            C best = -1;
+            int bi = k;
+            for (int rr = k + threadIdx.x; rr < b; rr += 32) {
+                C v = fabs(A[k * b + rr]);
+                if (v > best) {
+                    best = v;
+                    bi = rr;
+                }
+            }
+            for (int d = 16; d > 0; d >>= 1) {
+                C ob = __shfl_down_sync(0xffffffffu, best, d);
+                int oi = __shfl_down_sync(0xffffffffu, bi, d);
+                if (ob > best || (ob == best && oi < bi)) {
+                    best = ob;
+                    bi = oi;
+                }
+            }
+            if (threadIdx.x == 0) {
+                s_piv[k] = bi;
+                C pv = A[k * b + bi];
+                if (!(best > C(0))) {
+                    s_bad = 1;
+                    pv = C(1);
+                }
+                s_pinv = C(1) / pv;
+            }
+        }
+        __syncthreads();
+        const int p = s_piv[k];
+        const C pinv = s_pinv;
+        for (int t = threadIdx.x; t < 2 * b; t += blockDim.x) {
+            if (t < b) {
+                // column save (post-interchange view of column k)
+                const int rr = t;
+                const int src = (rr == k) ? p : (rr == p ? k : rr);
+                fcol[rr] = A[k * b + src];
+            } else {
+                const int cc = t - b;
+                if (cc == k) continue;
+                const C ak = A[cc * b + k], ap = A[cc * b + p];
+                A[cc * b + k] = ap * pinv;
+                if (p != k) A[cc * b + p] = ak;
+            }
+        }
+        __syncthreads();
+        if (act) {
+            if (r != k) {
+                const C f = fcol[r];
+                for (int cc = g; cc < b; cc += G)
+                    A[cc * b + r] = (cc == k) ? -f * pinv : A[cc * b + r] - f * A[cc * b + k];
+            } else if (g == 0) {
+                A[k * b + k] = pinv;
+            }
+        }
+        __syncthreads();
+    }
+    __shared__ int s_idx[IRK_MAX_GJ];
+    if (threadIdx.x == 0) {
+        for (int j = 0; j < b; ++j) s_idx[j] = j;
+        for (int kk = b - 1; kk >= 0; --kk) {
+            int q = s_piv[kk];
+            int t = s_idx[kk];
+            s_idx[kk] = s_idx[q];
+            s_idx[q] = t;
+        }
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        int j = e / b, rr = e - j * b;
+        Out[e] = A[s_idx[j] * b + rr];
+    }
+    __syncthreads();
+    return s_bad == 0;
+}
+
+// Register-tiled block product on shared-memory operands (column-major):
+// P = X Y, each thread owning a 4 x 2 tile of P (8 independent accumulation
+// chains).  mode 0: dst1 = P (and dst2 = P when dst2 != nullptr);
+// mode 1: dst1 -= P.
+template <class C>
+__device__ __forceinline__ void tile_gemm(C *dst1, C *dst2, const C *X, const C *Y, int b, int mode) {
+    const int nrt = (b + 3) / 4, nct = (b + 1) / 2;
+    for (int tile = threadIdx.x; tile < nrt * nct; tile += blockDim.x) {
+        const int r0 = (tile % nrt) * 4, c0 = (tile / nrt) * 2;
+        C acc[4][2];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = C(0);
+        const bool c1ok = c0 + 1 < b;
+        for (int t = 0; t < b; ++t) {
+            C xv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) xv[u] = (r0 + u < b) ? X[t * b + r0 + u] : C(0);
+            const C y0 = Y[c0 * b + t];
+            const C y1 = c1ok ? Y[(c0 + 1) * b + t] : C(0);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                acc[u][0] += xv[u] * y0;
+                acc[u][1] += xv[u] * y1;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (r0 + u >= b) continue;
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                if (v == 1 && !c1ok) continue;
+                const int e = (c0 + v) * b + r0 + u;
+                if (mode == 0) {
+                    dst1[e] = acc[u][v];
+                    if (dst2) dst2[e] = acc[u][v];
+                } else {
+                    dst1[e] -= acc[u][v];
+                }
+            }
+        }
+    }
+}
+
+// Load two b x b blocks from global memory into shared memory with every
+// thread's loads issued before its stores (one memory round trip).
+template <class C>
+__device__ __forceinline__ void load_pair(C *d1, const C *s1, C *d2, const C *s2, int bb) {
+    for (int e0 = threadIdx.x; e0 < bb; e0 += 4 * blockDim.x) {
+        C v1[4], v2[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            v1[u] = (e < bb) ? __ldg(s1 + e) : C(0);
+            v2[u] = (s2 && e < bb) ? __ldg(s2 + e) : C(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + u * blockDim.x;
+            if (e < bb) {
+                d1[e] = v1[u];
+                if (s2) d2[e] = v2[u];
+            }
+        }
+    }
+}
+
+// Factorisation of one level, fast path: four b x b shared buffers (X, Y, L,
+// D) + b.  D (the row's diagonal block) stays in shared memory for the whole
+// row; L_p = B_p D_i^{-1} is formed in shared memory and written once.
+template <class C>
+__global__ void __launch_bounds__(256) k_factor_level2(const int *rows, int b, const int *rp, const int *ci,
+                                                       const int *diag, const int *upd_ptr, const int *upd,
+                                                       C *vals, C *dinv, int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int bb = b * b;
+    C *X = reinterpret_cast<C *>(smem_raw);
+    C *Y = X + bb;
+    C *L = Y + bb;
+    C *D = L + bb;
+    C *fcol = D + bb;
+    const int R = rows[blockIdx.x];
+    const int dpos = diag[R];
+    load_pair<C>(D, vals + (long long)dpos * bb, nullptr, nullptr, bb);
+    for (int p = rp[R]; p < rp[R + 1]; ++p) {
+        const int i = ci[p];
+        if (i >= R) break;
+        load_pair<C>(X, vals + (long long)p * bb, Y, dinv + (long long)i * bb, bb);
+        __syncthreads();
+        tile_gemm<C>(L, vals + (long long)p * bb, X, Y, b, 0);  // L_p = B_p D_i^{-1}
+        __syncthreads();
+        for (int u = upd_ptr[p]; u < upd_ptr[p + 1]; ++u) {
+            const int q = upd[2 * u], pos = upd[2 * u + 1];
+            load_pair<C>(X, vals + (long long)pos * bb, nullptr, nullptr, bb);
+            __syncthreads();
+            tile_gemm<C>((q == dpos) ? D : vals + (long long)q * bb, nullptr, L, X, b, 1);  // B_q -= L_p B_pos
+            __syncthreads();
+        }
+    }
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) vals[(long long)dpos * bb + e] = D[e];
+    __syncthreads();
+    bool ok = gauss_jordan3(D, Y, b, fcol);
     for (int e = threadIdx.x; e < bb; e += blockDim.x) dinv[(long long)R * bb + e] = Y[e];
     if (!ok && threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_SINGULAR);
 }
@@ -889,15 +1086,24 @@ static int factor_impl(irk_ctx *c, double dt) {
     c->launches++;
     const int b = P.b;
     const size_t smem = (size_t)b * b * sizeof(C) * 2 + (size_t)b * sizeof(C);
-    if (smem > 48 * 1024)
+    const size_t smem4 = (size_t)b * b * sizeof(C) * 4 + (size_t)b * sizeof(C);
+    const bool fast = smem4 <= 227 * 1024;
+    if (fast && smem4 > 48 * 1024)
+        cudaFuncSetAttribute(k_factor_level2<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
+    if (!fast && smem > 48 * 1024)
         cudaFuncSetAttribute(k_factor_level<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     const int nlev = (int)P.lo_ptr.size() - 1;
     for (int l = 0; l < nlev; ++l) {
         int n = P.lo_ptr[l + 1] - P.lo_ptr[l];
         if (n <= 0) continue;
-        k_factor_level<C><<<n, 256, smem, c->stream>>>(P.d_lo_rows + P.lo_ptr[l], b, P.d_rp, P.d_ci, P.d_diag,
-                                                       P.d_upd_ptr, P.d_upd, (C *)P.d_vals, (C *)P.d_dinv,
-                                                       c->d_err);
+        if (fast)
+            k_factor_level2<C><<<n, 256, smem4, c->stream>>>(P.d_lo_rows + P.lo_ptr[l], b, P.d_rp, P.d_ci,
+                                                             P.d_diag, P.d_upd_ptr, P.d_upd, (C *)P.d_vals,
+                                                             (C *)P.d_dinv, c->d_err);
+        else
+            k_factor_level<C><<<n, 256, smem, c->stream>>>(P.d_lo_rows + P.lo_ptr[l], b, P.d_rp, P.d_ci,
+                                                           P.d_diag, P.d_upd_ptr, P.d_upd, (C *)P.d_vals,
+                                                           (C *)P.d_dinv, c->d_err);
         c->launches++;
     }
     if (c->fprec == IRK_FACTOR_BF16) {
