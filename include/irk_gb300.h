@@ -105,6 +105,16 @@ enum irk_formulation { IRK_TRANSFORMED = 0, IRK_UNTRANSFORMED = 1 };
  * block-triangular dependency graph. */
 enum irk_sweep_mode { IRK_SWEEP_AUTO = 0, IRK_SWEEP_LEVELS = 1 };
 
+/* Elimination order of the element blocks in the ILU(0) factorisation (the
+ * paper leaves the ordering open).  NATURAL: the input element order.
+ * MULTICOLOR: first-fit greedy colouring of the face-neighbour graph in
+ * input order, then elements sorted by (colour, index); on a two-colourable
+ * mesh every sweep has two levels.  A different order is a different
+ * preconditioner (same operator, same solution, other iteration count).
+ * Orderings and partitions apply to the stage-major kinds (UNCOUPLED,
+ * COUPLED); IRK_PC_ELEMENT accepts only the natural, unpartitioned form. */
+enum irk_ordering { IRK_ORDER_NATURAL = 0, IRK_ORDER_MULTICOLOR = 1 };
+
 typedef struct {
     int restart;       /* GMRES restart length (default 30) */
     int max_iter;      /* total inner iterations (default 3000) */
@@ -119,6 +129,12 @@ typedef struct {
     int timing;        /* 1: time each phase of irk_factor / irk_solve with CUDA
                           events on the context's stream (see irk_stats); default 0 */
     int sweep;         /* enum irk_sweep_mode: how the preconditioner sweeps run */
+    int ordering;      /* enum irk_ordering: elimination order of the ILU(0) */
+    int partitions;    /* > 1: partitioned ILU(0) (Sec. 4.5) with this many
+                          contiguous ranges of element indices; 0/1: none */
+    const int32_t *partition; /* optional host array of T partition ids (overrides
+                          partitions); blocks coupling two different ids are
+                          dropped from the preconditioner; copied at irk_setup */
 } irk_options;
 
 /* Fill *opt with the defaults listed above. */

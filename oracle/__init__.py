@@ -78,6 +78,11 @@ def _load():
             lib.irk_ref_solve.argtypes = [I, I, P, P, I, I, P, P, P, L, P, D, I, P, I, I, D, P, P,
                                           P, P, P, P]
             lib.irk_ref_precond_apply.argtypes = [I, I, P, P, I, I, P, P, P, L, P, D, I, P, P, P]
+            lib.irk_ref_assemble_ordered.argtypes = [I, I, P, P, P, P, D, D, P, P, P, P, P]
+            lib.irk_ref_assemble_ordered.restype = L
+            lib.irk_ref_solve_ordered.argtypes = [I, P, I, I, P, P, P, L, P, D, P, P, P, I, I, D, P, P, P,
+                                                  P, P]
+            lib.irk_ref_precond_apply_ordered.argtypes = [I, P, I, I, P, P, P, L, P, D, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -177,6 +182,54 @@ class Problem:
                                          rp, ci, J, js, M, float(dt), precond, _p(sh), _p(v),
                                          _p(z)), "precond")
         return z
+
+    # --- reordered / partitioned uncoupled preconditioner (Sec. 4.5) -------
+    def solve_ordered(self, R, dt, perm=None, part=None, rtol=1e-8, shift=None, restart=30,
+                      max_iter=3000):
+        lib = _load()
+        R = _f64(R).reshape(-1)
+        X = np.zeros_like(R)
+        it, cyc, rr = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+        pm = None if perm is None else _i32(perm)
+        pt = None if part is None else _i32(part)
+        sh = None if shift is None else _f64(shift)
+        rp, ci, J, js, M = self._args()
+        rc = lib.irk_ref_solve_ordered(self.s, _p(self.Ainv), self.T, self.m, rp, ci, J, js, M,
+                                       float(dt), _p(sh), _p(pm), _p(pt), restart, max_iter,
+                                       float(rtol), _p(R), _p(X), ctypes.byref(it), ctypes.byref(rr),
+                                       ctypes.byref(cyc))
+        _check(rc, "solve_ordered")
+        return dict(x=X, iters=it.value, relres=rr.value, cycles=cyc.value, rc=rc)
+
+    def precond_apply_ordered(self, v, dt, perm=None, part=None, shift=None):
+        lib = _load()
+        v = _f64(v).reshape(-1)
+        z = np.empty_like(v)
+        pm = None if perm is None else _i32(perm)
+        pt = None if part is None else _i32(part)
+        sh = None if shift is None else _f64(shift)
+        rp, ci, J, js, M = self._args()
+        _check(lib.irk_ref_precond_apply_ordered(self.s, _p(self.Ainv), self.T, self.m, rp, ci, J, js, M,
+                                                 float(dt), _p(sh), _p(pm), _p(pt), _p(v), _p(z)),
+               "precond_apply_ordered")
+        return z
+
+    def assemble_ordered(self, k, d, dt, perm=None, part=None):
+        lib = _load()
+        mm = self.m * self.m
+        nnzb = int(self.row_ptr[-1])
+        Jk = self.J[k * self.jstride: k * self.jstride + nnzb * mm] if self.jstride else self.J
+        Jk = np.ascontiguousarray(Jk)
+        pm = None if perm is None else _i32(perm)
+        pt = None if part is None else _i32(part)
+        args = (self.T, self.m, _p(self.row_ptr), _p(self.col_idx), _p(Jk), _p(self.M), float(d), float(dt),
+                _p(pm), _p(pt))
+        nb = lib.irk_ref_assemble_ordered(*args, None, None, None)
+        rp = np.zeros(self.T + 1, np.int32)
+        ci = np.zeros(nb, np.int32)
+        vals = np.zeros(nb * mm)
+        lib.irk_ref_assemble_ordered(*args, _p(rp), _p(ci), _p(vals))
+        return rp, ci, vals.reshape(nb, self.m, self.m)
 
     # --- assembled forms (for pins) ---------------------------------------
     def assemble_stage_major(self, dt, form=FORM_TRANSFORMED):

@@ -798,3 +798,153 @@ int irk_ref_precond_apply(int form, int s, const double *A, const double *Ainv, 
     ref_precond_free(&pc);
     return rc;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 4.5: reordered and partitioned stage-uncoupled block ILU(0).         */
+/* ------------------------------------------------------------------------ */
+
+/* Build, for one stage, the shifted matrix d M - dt J_k restricted to the
+ * blocks whose two elements share a partition (part[i] == part[j]; part NULL
+ * = one partition), with the elements renumbered so that element perm[q] is
+ * the q-th eliminated (perm NULL = natural order).  Returns the number of
+ * blocks; with out_rp == NULL only counts. */
+long irk_ref_assemble_ordered(int T, int m, const int *row_ptr, const int *col_idx, const double *Jk,
+                              const double *M, double d, double dt, const int *perm, const int *part,
+                              int *out_rp, int *out_ci, double *out_vals)
+{
+    long mm = (long)m * m;
+    int *inv = (int *)malloc(sizeof(int) * (T > 0 ? T : 1));
+    if (!inv) return -1;
+    for (int q = 0; q < T; ++q) inv[perm ? perm[q] : q] = q;
+    long pos = 0;
+    for (int q = 0; q < T; ++q) {
+        int e = perm ? perm[q] : q;
+        if (out_rp) out_rp[q] = (int)pos;
+        /* neighbours of e kept in the preconditioner, in increasing new index */
+        int cnt = 0;
+        int cols[64];
+        long src[64];
+        for (long p = row_ptr[e]; p < row_ptr[e + 1]; ++p) {
+            int j = col_idx[p];
+            if (part && part[j] != part[e]) continue;
+            if (cnt >= 64) { free(inv); return -1; }
+            cols[cnt] = inv[j];
+            src[cnt] = p;
+            ++cnt;
+        }
+        for (int a = 1; a < cnt; ++a) /* insertion sort by new column */
+            for (int b2 = a; b2 > 0 && cols[b2 - 1] > cols[b2]; --b2) {
+                int tc = cols[b2]; cols[b2] = cols[b2 - 1]; cols[b2 - 1] = tc;
+                long ts = src[b2]; src[b2] = src[b2 - 1]; src[b2 - 1] = ts;
+            }
+        for (int a = 0; a < cnt; ++a) {
+            if (out_rp) {
+                out_ci[pos] = cols[a];
+                double *blk = out_vals + pos * mm;
+                int j = col_idx[src[a]];
+                for (long x = 0; x < mm; ++x)
+                    blk[x] = (j == e ? d * M[(long)e * mm + x] : 0.0) - dt * Jk[src[a] * mm + x];
+            }
+            ++pos;
+        }
+    }
+    if (out_rp) out_rp[T] = (int)pos;
+    free(inv);
+    return pos;
+}
+
+typedef struct {
+    int s, T, m;
+    const int *perm;
+    int *rp, *ci; /* one pattern shared by the stages */
+    double *vals, *dlu;
+    int *dpiv;
+    long nnzb;
+    double *work, *work2;
+} ref_ordered_pc;
+
+static void ref_ordered_apply(void *ctx, const double *v, double *z)
+{
+    ref_ordered_pc *p = (ref_ordered_pc *)ctx;
+    long n = (long)p->T * p->m;
+    long mm = (long)p->m * p->m;
+    for (int k = 0; k < p->s; ++k) {
+        for (int q = 0; q < p->T; ++q) {
+            int e = p->perm ? p->perm[q] : q;
+            memcpy(p->work + (long)q * p->m, v + k * n + (long)e * p->m, sizeof(double) * p->m);
+        }
+        irk_ref_bilu0_apply(p->T, p->m, p->rp, p->ci, p->vals + k * p->nnzb * mm,
+                            p->dlu + (long)k * p->T * mm, p->dpiv + (long)k * p->T * p->m, p->work, p->work2);
+        for (int q = 0; q < p->T; ++q) {
+            int e = p->perm ? p->perm[q] : q;
+            memcpy(z + k * n + (long)e * p->m, p->work2 + (long)q * p->m, sizeof(double) * p->m);
+        }
+    }
+}
+
+static void ref_ordered_free(ref_ordered_pc *p)
+{
+    free(p->rp); free(p->ci); free(p->vals); free(p->dlu); free(p->dpiv); free(p->work); free(p->work2);
+}
+
+static int ref_ordered_build(ref_ordered_pc *p, int s, const double *Ainv, int T, int m,
+                             const int *row_ptr, const int *col_idx, const double *J, long jstride,
+                             const double *M, double dt, const double *shift, const int *perm,
+                             const int *part)
+{
+    memset(p, 0, sizeof(*p));
+    p->s = s; p->T = T; p->m = m; p->perm = perm;
+    long mm = (long)m * m;
+    double alpha[64];
+    if (s > 64) return REF_EINVAL;
+    if (shift) memcpy(alpha, shift, sizeof(double) * s);
+    else irk_ref_shift_column_rule(s, Ainv, alpha);
+    long nb = irk_ref_assemble_ordered(T, m, row_ptr, col_idx, J, M, 0.0, dt, perm, part, NULL, NULL, NULL);
+    if (nb < 0) return REF_EINVAL;
+    p->nnzb = nb;
+    p->rp = (int *)malloc(sizeof(int) * (T + 1));
+    p->ci = (int *)malloc(sizeof(int) * (nb > 0 ? nb : 1));
+    p->vals = (double *)malloc(sizeof(double) * s * nb * mm);
+    p->dlu = (double *)malloc(sizeof(double) * s * T * mm);
+    p->dpiv = (int *)malloc(sizeof(int) * s * T * m);
+    p->work = (double *)malloc(sizeof(double) * T * m);
+    p->work2 = (double *)malloc(sizeof(double) * T * m);
+    if (!p->rp || !p->ci || !p->vals || !p->dlu || !p->dpiv || !p->work || !p->work2) return REF_ENOMEM;
+    for (int k = 0; k < s; ++k) {
+        double *vk = p->vals + k * nb * mm;
+        irk_ref_assemble_ordered(T, m, row_ptr, col_idx, J + k * jstride, M, Ainv[k * s + k] + alpha[k], dt,
+                                 perm, part, p->rp, p->ci, vk);
+        int rc = irk_ref_bilu0(T, m, p->rp, p->ci, vk, p->dlu + (long)k * T * mm, p->dpiv + (long)k * T * m);
+        if (rc != REF_OK) return rc;
+    }
+    return REF_OK;
+}
+
+/* Transformed solve (eq. big-irk) with the reordered / partitioned
+ * stage-uncoupled preconditioner. */
+int irk_ref_solve_ordered(int s, const double *Ainv, int T, int m, const int *row_ptr, const int *col_idx,
+                          const double *J, long jstride, const double *M, double dt, const double *shift,
+                          const int *perm, const int *part, int restart, int max_iter, double rtol,
+                          const double *R, double *X, int *iters, double *relres, int *cycles)
+{
+    ref_operator op = {0, s, T, m, Ainv, row_ptr, col_idx, J, M, jstride, dt};
+    ref_ordered_pc pc;
+    int rc = ref_ordered_build(&pc, s, Ainv, T, m, row_ptr, col_idx, J, jstride, M, dt, shift, perm, part);
+    if (rc == REF_OK)
+        rc = irk_ref_fgmres((long)s * T * m, ref_operator_apply, &op, ref_ordered_apply, &pc, R, X, rtol,
+                            restart, max_iter, iters, relres, NULL, cycles);
+    ref_ordered_free(&pc);
+    return rc;
+}
+
+int irk_ref_precond_apply_ordered(int s, const double *Ainv, int T, int m, const int *row_ptr,
+                                  const int *col_idx, const double *J, long jstride, const double *M,
+                                  double dt, const double *shift, const int *perm, const int *part,
+                                  const double *v, double *z)
+{
+    ref_ordered_pc pc;
+    int rc = ref_ordered_build(&pc, s, Ainv, T, m, row_ptr, col_idx, J, jstride, M, dt, shift, perm, part);
+    if (rc == REF_OK) ref_ordered_apply(&pc, v, z);
+    ref_ordered_free(&pc);
+    return rc;
+}

@@ -252,6 +252,9 @@ void irk_default_options(irk_options *o) {
     o->stream = nullptr;
     o->timing = 0;
     o->sweep = IRK_SWEEP_AUTO;
+    o->ordering = IRK_ORDER_NATURAL;
+    o->partitions = 0;
+    o->partition = nullptr;
 }
 
 const char *irk_strerror(int code) {
@@ -283,11 +286,13 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
     irk_default_options(&c->opt);
     if (opt) c->opt = *opt;
     c->opt.shift = nullptr;
+    c->opt.partition = nullptr;
     int rc = IRK_OK;
     if (c->opt.restart < 1 || c->opt.restart > IRK_MAX_RESTART || c->opt.max_iter < 0 ||
         c->opt.precond < IRK_PC_NONE || c->opt.precond > IRK_PC_ELEMENT || c->opt.factor_prec < 0 ||
         c->opt.factor_prec > IRK_FACTOR_BF16 || c->opt.krylov_arith < 0 || c->opt.krylov_arith > 1 ||
         c->opt.formulation < 0 || c->opt.formulation > 1 || c->opt.sweep < 0 || c->opt.sweep > 1 ||
+        c->opt.ordering < 0 || c->opt.ordering > 1 || c->opt.partitions < 0 ||
         (c->opt.precond == IRK_PC_UNCOUPLED && c->opt.formulation != IRK_TRANSFORMED)) {
         delete c;
         return IRK_ERR_INVALID;
@@ -341,6 +346,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
         free_ctx(c);
         return rc;
     }
+    if (opt && opt->partition) c->h_part.assign(opt->partition, opt->partition + T);
     // tableau, inverse, shifts (Sec. 4.3.2 column rule unless given)
     if (A) {
         memcpy(c->A, A, sizeof(double) * s * s);

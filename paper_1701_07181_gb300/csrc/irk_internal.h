@@ -73,6 +73,7 @@ struct irk_ctx {
     int df = 0;  // 1: Krylov arithmetic is double-float
     int fprec = IRK_FACTOR_FP64;
     std::vector<int> h_rp, h_ci;
+    std::vector<int> h_part;  // optional partition id per element (Sec. 4.5)
     int *d_rp = nullptr, *d_ci = nullptr;
     vec8 *d_J = nullptr;  // nnzb blocks, column-major, binary64 or double-float
     vec8 *d_M = nullptr;  // T blocks, column-major

@@ -935,39 +935,75 @@ int pc_build_pattern(irk_ctx *c) {
     const bool transformed = c->opt.formulation == IRK_TRANSFORMED;
     const std::vector<int> &rp = c->h_rp, &ci = c->h_ci;
     HostPattern h;
+    // elimination order (perm[q] = element eliminated q-th) and partitions
+    std::vector<int> perm(T), inv(T), part;
+    for (int q = 0; q < T; ++q) perm[q] = q;
+    if (c->opt.ordering == IRK_ORDER_MULTICOLOR) {
+        std::vector<int> colour(T, -1);
+        std::vector<char> used;
+        for (int i = 0; i < T; ++i) {  // first-fit colouring in input order
+            used.assign(rp[i + 1] - rp[i] + 2, 0);
+            for (int p = rp[i]; p < rp[i + 1]; ++p) {
+                int j = ci[p];
+                if (j != i && colour[j] >= 0 && colour[j] < (int)used.size()) used[colour[j]] = 1;
+            }
+            int cc = 0;
+            while (used[cc]) ++cc;
+            colour[i] = cc;
+        }
+        std::stable_sort(perm.begin(), perm.end(), [&](int x, int y) { return colour[x] < colour[y]; });
+    }
+    for (int q = 0; q < T; ++q) inv[perm[q]] = q;
+    if (!c->h_part.empty()) {
+        part = c->h_part;
+    } else if (c->opt.partitions > 1) {
+        part.resize(T);
+        for (int i = 0; i < T; ++i) part[i] = (int)((long long)i * c->opt.partitions / T);
+    }
+    const bool reordered = c->opt.ordering != IRK_ORDER_NATURAL || !part.empty();
     if (P.kind == IRK_PC_UNCOUPLED || P.kind == IRK_PC_COUPLED) {
         if (P.kind == IRK_PC_UNCOUPLED && !transformed) return IRK_ERR_INVALID;
         h.nb = s * T;
         h.b = m;
         h.rp.push_back(0);
+        std::vector<std::pair<int, int>> nb_new;  // (new index, J position) of kept neighbours
         for (int k = 0; k < s; ++k)
-            for (int i = 0; i < T; ++i) {
-                auto mass = [&](int l) {  // block (k,i)-(l,i), mass coupling
-                    h.ci.push_back(l * T + i);
-                    h.asmv.push_back(AsmEntry{-1, i, k * s + l, 0});
+            for (int q = 0; q < T; ++q) {
+                const int e = perm[q];
+                nb_new.clear();
+                for (int p = rp[e]; p < rp[e + 1]; ++p) {
+                    const int j = ci[p];
+                    if (!part.empty() && part[j] != part[e]) continue;
+                    nb_new.push_back(std::make_pair(inv[j], p));
+                }
+                std::sort(nb_new.begin(), nb_new.end());
+                auto mass = [&](int l) {  // block (k,e)-(l,e), mass coupling
+                    h.ci.push_back(l * T + q);
+                    h.asmv.push_back(AsmEntry{-1, e, k * s + l, 0});
                 };
                 if (P.kind == IRK_PC_COUPLED && transformed)
                     for (int l = 0; l < k; ++l) mass(l);
                 int lfirst = (P.kind == IRK_PC_COUPLED && !transformed) ? 0 : k;
                 int llast = (P.kind == IRK_PC_COUPLED && !transformed) ? s - 1 : k;
                 for (int l = lfirst; l <= llast; ++l)
-                    for (int p = rp[i]; p < rp[i + 1]; ++p) {
-                        int j = ci[p];
-                        h.ci.push_back(l * T + j);
+                    for (const auto &nq : nb_new) {
+                        const int p = nq.second, j = ci[p];
+                        h.ci.push_back(l * T + nq.first);
                         if (transformed)  // d_k M - dt J  (uncoupled: d_k = A^{-1}_kk + alpha_k)
-                            h.asmv.push_back(AsmEntry{p, j == i ? i : -1, k * s + k, 0});
-                        else  // [k==l][i==j] M - dt a_kl J
-                            h.asmv.push_back(AsmEntry{p, (j == i && l == k) ? i : -1, 0, k * s + l});
+                            h.asmv.push_back(AsmEntry{p, j == e ? e : -1, k * s + k, 0});
+                        else  // [k==l][e==j] M - dt a_kl J
+                            h.asmv.push_back(AsmEntry{p, (j == e && l == k) ? e : -1, 0, k * s + l});
                     }
                 if (P.kind == IRK_PC_COUPLED && transformed)
                     for (int l = k + 1; l < s; ++l) mass(l);
                 h.rp.push_back((int)h.ci.size());
             }
         for (int R = 0; R < h.nb; ++R) {
-            int k = R / T, i = R - k * T;
-            h.voff.push_back((i * s + k) * m);
+            int k = R / T, q = R - k * T;
+            h.voff.push_back((perm[q] * s + k) * m);
         }
     } else if (P.kind == IRK_PC_ELEMENT) {
+        if (reordered) return IRK_ERR_INVALID;
         h.nb = T;
         h.b = s * m;
         h.rp = rp;

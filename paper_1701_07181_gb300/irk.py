@@ -38,7 +38,9 @@ class Options(ctypes.Structure):
     _fields_ = [("restart", ctypes.c_int), ("max_iter", ctypes.c_int), ("precond", ctypes.c_int),
                 ("factor_prec", ctypes.c_int), ("krylov_arith", ctypes.c_int),
                 ("formulation", ctypes.c_int), ("shift", ctypes.POINTER(ctypes.c_double)),
-                ("stream", ctypes.c_void_p), ("timing", ctypes.c_int), ("sweep", ctypes.c_int)]
+                ("stream", ctypes.c_void_p), ("timing", ctypes.c_int), ("sweep", ctypes.c_int),
+                ("ordering", ctypes.c_int), ("partitions", ctypes.c_int),
+                ("partition", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Stats(ctypes.Structure):
@@ -111,7 +113,8 @@ class Solver:
 
     def __init__(self, s, T, m, row_ptr, col_idx, J, M, A=None, precond="uncoupled",
                  factor_prec="fp64", krylov="fp64", formulation="transformed", restart=30,
-                 max_iter=3000, shift=None, stream=None, timing=False, sweep="auto"):
+                 max_iter=3000, shift=None, stream=None, timing=False, sweep="auto",
+                 ordering="natural", partitions=0, partition=None):
         lib = load()
         self._lib = lib
         self.s, self.T, self.m = int(s), int(T), int(m)
@@ -132,6 +135,12 @@ class Solver:
             opt.stream = ctypes.c_void_p(int(stream))
         opt.timing = 1 if timing else 0
         opt.sweep = {"auto": 0, "levels": 1}[sweep]
+        opt.ordering = {"natural": 0, "multicolor": 1}[ordering]
+        opt.partitions = int(partitions)
+        self._part = None
+        if partition is not None:
+            self._part = np.ascontiguousarray(partition, dtype=np.int32)
+            opt.partition = self._part.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         self._opt = opt
         rp, k1, sp1 = _ptr(row_ptr, np.int32)
         ci, k2, sp2 = _ptr(col_idx, np.int32)
