@@ -6,7 +6,8 @@ preconditioner is rebuilt once per linear solve) for each dt in
 {0.01, 0.1, 1} of the 2D workload T=20000 triangles (periodic 100x100 split
 grid, r=3), p=3 (m=40), Radau IIA s=3, synthetic seeded DG-shaped blocks.
 Solver: FGMRES(30), double-float Krylov arithmetic on the FP32 pipe, shifted
-stage-uncoupled block ILU(0) with FP32 factors, all stages per launch.
+stage-uncoupled block ILU(0) with FP32 factors in two-colour element order,
+all stages per launch.
 
 Reported beside it: the plain FP64 GPU path (FP64 factors and Krylov, one
 request at a time), per-phase device times with roofline fractions, the
@@ -41,6 +42,8 @@ METRIC = "IRK stage-system solves/s at rtol 1e-8"
 UNIT = "solves/s"
 WORKLOAD = ("2D periodic 100x100 split grid, T=20000 triangles, r=3, p=3 (m=40), Radau IIA s=3, "
             "dt in {0.01,0.1,1}, FGMRES(30) rtol 1e-8, shifted uncoupled block ILU(0)")
+SOLVER = ("double-float Krylov, FP32 factors, shifted uncoupled block ILU(0) in two-colour order "
+          "(all stages per launch, persistent sweeps)")
 
 
 def algorithmic_bytes(T, m, r, s):
@@ -123,6 +126,21 @@ class Clocks:
         reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
                 "reasons": reasons, "samples": len(rows)}
+
+
+def replica_aggregate(local_ms, local_solves, dist=None, device=None):
+    """Whole-job throughput of independent replicas: solves of all ranks
+    divided by the slowest rank's time (max over ranks).  Returns
+    (value, max_ms, total_solves)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return local_solves / (local_ms / 1000.0), local_ms, local_solves
+    import torch
+    t = torch.tensor([float(local_ms)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(local_solves)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    max_ms, total = float(t.item()), float(n.item())
+    return total / (max_ms / 1000.0), max_ms, total
 
 
 def dist_env():
@@ -230,7 +248,7 @@ def main():
     rp, ci, J, M, R = t(P.row_ptr), t(P.col_idx), t(P.J), t(P.M), t(P.R)
     W = torch.empty_like(R)
     S = irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec="fp32", krylov="df64",
-                   timing=True)
+                   timing=True, ordering="multicolor")
 
     def step(solver, acc=None):
         for dt in DTS:
@@ -272,9 +290,7 @@ def main():
     e1.record()
     barrier()
     clk = clocks.stop()
-    ms = max_over_ranks(e0.elapsed_time(e1))
-    solves = world * args.steps * len(DTS)
-    value = solves / (ms / 1000.0)
+    value, ms, solves = replica_aggregate(e0.elapsed_time(e1), args.steps * len(DTS), dist, dev)
 
     # end to end through host buffers (pinned), inputs copied in and the
     # result copied out on every solve
@@ -293,6 +309,22 @@ def main():
            "d2h_bytes_per_step": len(DTS) * R.numel() * 8}
     st_last = S.stats()
     S.close()
+
+    # the same mixed path with the ILU(0) in the input (natural) element order
+    Sn = irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec="fp32", krylov="df64")
+    step(Sn)  # warm-up
+    nat_acc = dict(launches=0, iters=[], matvec_ms=0.0, precond_ms=0.0, ortho_ms=0.0, factor_ms=0.0,
+                   solve_ms=0.0, n_matvec=0, n_precond=0, n_ortho=0)
+    barrier()
+    n0, n1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0.record()
+    for _ in range(args.plain_steps):
+        step(Sn, nat_acc)
+    n1.record()
+    barrier()
+    nat_ms = max_over_ranks(n0.elapsed_time(n1))
+    nat_value = world * args.plain_steps * len(DTS) / (nat_ms / 1000.0)
+    Sn.close()
 
     # plain FP64 GPU path, one request at a time
     Sp = irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec="fp64", krylov="fp64")
@@ -336,11 +368,14 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "df64 Krylov / f32 factors",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "solves_per_step": len(DTS), "l2": "inputs larger than L2 "
+            "config": {"workload": WORKLOAD, "solver": SOLVER, "solves_per_step": len(DTS),
+                       "l2": "inputs larger than L2 "
                        "(J alone 1.0 GB per rank)", "parallelism": "replicas x%d" % world,
                        "iters_per_solve": acc["iters"][: len(DTS)]},
             "plain_fp64_gpu": {"value": plain_value, "unit": UNIT, "iters_per_solve": plain_acc["iters"],
+                               "solver": "binary64 Krylov and factors, natural order",
                                "speedup_of_value": value / plain_value},
+            "natural_order_mixed": {"value": nat_value, "unit": UNIT, "iters_per_solve": nat_acc["iters"]},
             "roofline": roofline, "kernels": kernels, "e2e": e2e,
             "gpu_launches": acc["launches"], "clocks": clk,
             "last_solve": {"iters": st_last["iters"], "relres": st_last["relres"]}}
