@@ -220,6 +220,59 @@ IRK_API int irk_apply_precond(irk_ctx *ctx, const double *V, double *Z, int mem_
 #define IRK_NOALLOC_SCRATCH_BYTES (64u << 20)
 IRK_API int irk_apply_precond_noalloc(irk_ctx *ctx, const double *V, double *Z, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Multi-request engine (continuous batching).
+ *
+ * An irk_group holds many independent stage systems (one per request: its
+ * own mesh pattern, J, M, right-hand side, dt and rtol) of one class --
+ * same s, Butcher matrix, block size m and options -- in device pools sized
+ * at creation.  irk_group_step advances every active request by one FGMRES
+ * iteration with one launch per phase for all of them (the operator product
+ * of all requests, one persistent sweep over the level-merged rows of all
+ * requests, Gram-Schmidt with per-request deterministic reductions, Givens
+ * rotations per request).  Requests are submitted and collected between
+ * steps: a request that arrives while others are being solved joins at the
+ * next step, and a finished request frees its pools for the next.
+ * Each request follows exactly the algorithm of irk_solve (same
+ * preconditioner, same stopping test); only its floating-point reductions
+ * are partitioned differently, so its result matches irk_solve within the
+ * solve tolerance.  Preconditioners: IRK_PC_UNCOUPLED or IRK_PC_NONE;
+ * factors FP32 or FP64; any ordering; formulation transformed.
+ * ------------------------------------------------------------------------ */
+typedef struct irk_group irk_group;
+
+/* max_elements / max_blocks: capacity in elements and J blocks summed over the
+ * requests held at once; max_requests: most requests held at once. */
+IRK_API int irk_group_create(irk_group **out, int s, const double *A, int m, int max_elements,
+                             int max_blocks, int max_requests, const irk_options *opt);
+
+/* Admit one request (copies everything; factors it for dt on the device).
+ * Layouts as for irk_setup / irk_solve (R stage-major), in mem_space.
+ * Returns IRK_ERR_NOMEM when the pools cannot hold it now (retry after a
+ * request has been collected); *slot receives the request's handle. */
+IRK_API int irk_group_submit(irk_group *g, int T, const int32_t *row_ptr, const int32_t *col_idx,
+                             const double *J, const double *M, const double *R, double dt,
+                             double rtol, int mem_space, int *slot);
+
+/* One FGMRES iteration for every active request (plus the residual and
+ * restart bookkeeping of requests at a cycle boundary).  *n_active receives
+ * the number of requests not yet finished. */
+IRK_API int irk_group_step(irk_group *g, int *n_active);
+
+/* State of a request: returns 1 while it runs, 0 when finished (its result
+ * may be collected), or an error code.  iters / relres / status may be NULL;
+ * status receives IRK_OK, IRK_NOT_CONVERGED or an error of the request. */
+IRK_API int irk_group_query(const irk_group *g, int slot, int *iters, double *relres, int *status);
+
+/* Copy a finished request's W (s*T*m, stage-major) to mem_space and free its
+ * slot and pools. */
+IRK_API int irk_group_collect(irk_group *g, int slot, double *W, int mem_space);
+
+/* Device bytes the group holds (pools and work arrays). */
+IRK_API long long irk_group_device_bytes(const irk_group *g);
+
+IRK_API void irk_group_destroy(irk_group *g);
+
 /* Counters of the last irk_factor / irk_solve (host values). */
 typedef struct {
     int iters, cycles, levels_lower, levels_upper;

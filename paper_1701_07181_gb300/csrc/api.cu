@@ -238,6 +238,10 @@ void free_ctx(irk_ctx *c) {
 
 }  // namespace
 
+// tableau helpers shared with the multi-request engine (group.cu)
+bool irk_radau_iia_tableau(int s, double *A) { return radau_iia(s, A); }
+bool irk_invert_small(int n, const double *A, double *X) { return invert_small(n, A, X); }
+
 extern "C" {
 
 void irk_default_options(irk_options *o) {

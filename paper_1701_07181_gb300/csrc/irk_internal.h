@@ -136,5 +136,16 @@ int pc_factor(irk_ctx *c, double dt);
 int pc_apply(irk_ctx *c, const vec8 *v, vec8 *z);
 void pc_free(PcSystem &p);
 
+// ---- used by the multi-request engine (group.cu), defined in k_ilu.cu ----
+int ilu_assemble(cudaStream_t st, int fprec, long long nnz, int m, const AsmEntry *ent, const vec8 *J,
+                 const vec8 *M, int df, const double *cm, int ncm, const double *cj, int ncj, void *vals);
+int ilu_factor_level(cudaStream_t st, int fprec, const int *rows, int nrows, int b, const int *rp, const int *ci,
+                     const int *diag, const int *upd_ptr, const int *upd, void *vals, void *dinv, int *err);
+int ilu_sweep_group(cudaStream_t st, int dev, int fprec, int df, int nitems, int b, int max_item_blocks,
+                    const int *lo, const int *up, const int *rp, const int *ci, const int *voff, const void *vals,
+                    const void *dinv, vec8 *vpool, unsigned long long *llpool, int ep, int *err,
+                    const int *lane_of_row, const long long *vin, const long long *zout, const long long *yll,
+                    const long long *zll);
+
 // ---- helpers (api.cu) ----
 int cuda_status(cudaError_t e);

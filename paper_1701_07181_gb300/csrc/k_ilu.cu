@@ -708,11 +708,20 @@ __device__ __forceinline__ bool ll_wait_row(const unsigned long long *row, int b
 // the dependency of block k is published and the copy of block k landed,
 // refilling the slot with block k + NS.  y (forward results) and zc
 // (backward results) are published as self-validating words.
+// Group mode (lane_of_row != nullptr): rows belong to independent requests
+// ("lanes"); voff is lane-local and each lane's vectors and published words
+// start at its own offsets (lane_vin < 0: the lane sits this launch out).
+struct SweepLanes {
+    const int *lane_of_row;
+    const long long *vin, *zout, *yll, *zll;
+};
+
 template <class AR, class C, class F>
 __global__ void __launch_bounds__(128) k_sweep_staged(int nb, int b, int NS, const int *lo_rows, const int *up_rows,
                                                       const int *rp, const int *ci, const int *voff, const F *vals,
                                                       const F *dinv, const vec8 *v, unsigned long long *yll,
-                                                      unsigned long long *zll, vec8 *z, int ep, int *err) {
+                                                      unsigned long long *zll, vec8 *z, int ep, int *err,
+                                                      SweepLanes lanes) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int bb = b * b;
@@ -737,10 +746,22 @@ __global__ void __launch_bounds__(128) k_sweep_staged(int nb, int b, int NS, con
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const unsigned FULL = 0xffffffffu;
     constexpr int LW = LL<C>::W;
+    const vec8 *v0 = v;
+    vec8 *z0 = z;
+    unsigned long long *y0 = yll, *zz0 = zll;
     for (int q = gw; q < 2 * nb; q += W) {
         const bool fwd = q < nb;
         const int R = fwd ? lo_rows[q] : up_rows[q - nb];
         const int vo = voff[R];
+        if (lanes.lane_of_row) {
+            const int ln = lanes.lane_of_row[R];
+            const long long vb = lanes.vin[ln];
+            if (vb < 0) continue;  // warp-uniform: the whole item is skipped
+            v = v0 + vb;
+            z = z0 + lanes.zout[ln];
+            yll = y0 + lanes.yll[ln];
+            zll = zz0 + lanes.zll[ln];
+        }
         int pbeg, pend, nblk;
         if (fwd) {
             pbeg = rp[R];
@@ -1183,7 +1204,8 @@ static int apply_persistent(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, c
     const int *lo = P.d_lo_rows, *up = P.d_up_rows, *rp = P.d_rp, *ci = P.d_ci, *vo = P.d_voff;
     unsigned long long *yll = P.d_yll, *zll = P.d_zll;
     int *err = c->d_err;
-    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &vo, &vals, &dinv, &v, &yll, &zll, &z, &ep, &err};
+    SweepLanes none = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &vo, &vals, &dinv, &v, &yll, &zll, &z, &ep, &err, &none};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, P.coop_blocks, threads, args, smem, c->stream);
     c->launches++;
     return cuda_status(e);
@@ -1290,7 +1312,8 @@ int na_sweep(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv, u
     int grid = per_sm * sms;
     int nb = P.nb, b = P.b, ep = 1;
     const int *lo = P.d_lo_rows, *up = P.d_up_rows, *rp = P.d_rp, *ci = P.d_ci, *vo = P.d_voff;
-    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &vo, &vals, &dinv, &v, &yll, &zll, &z, &ep, &err};
+    SweepLanes none = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &vo, &vals, &dinv, &v, &yll, &zll, &z, &ep, &err, &none};
     return cuda_status(cudaLaunchCooperativeKernel((const void *)kern, grid, threads, args, smem, st));
 }
 
@@ -1361,4 +1384,91 @@ extern "C" int irk_apply_precond_noalloc(irk_ctx *c, const double *V, double *Z,
     if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
     if (!rc && (herr & IRK_DEV_ERR_TIMEOUT)) rc = IRK_ERR_TIMEOUT;
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers used by the multi-request engine (group.cu): the same kernels on
+// caller-provided arrays.
+int ilu_assemble(cudaStream_t st, int fprec, long long nnz, int m, const AsmEntry *ent, const vec8 *J,
+                 const vec8 *M, int df, const double *cm, int ncm, const double *cj, int ncj, void *vals) {
+    AsmTables tab;
+    memset(&tab, 0, sizeof(tab));
+    for (int q = 0; q < ncm && q < IRK_MAX_S * IRK_MAX_S; ++q) tab.cm[q] = cm[q];
+    for (int q = 0; q < ncj && q < IRK_MAX_S * IRK_MAX_S; ++q) tab.cj[q] = cj[q];
+    const int g = grid_cap(nnz * m * m);
+    if (fprec == IRK_FACTOR_FP64)
+        k_assemble<double><<<g, 256, 0, st>>>(nnz, m, ent, J, M, df, tab, (double *)vals);
+    else
+        k_assemble<float><<<g, 256, 0, st>>>(nnz, m, ent, J, M, df, tab, (float *)vals);
+    return cuda_status(cudaGetLastError());
+}
+
+int ilu_factor_level(cudaStream_t st, int fprec, const int *rows, int nrows, int b, const int *rp, const int *ci,
+                     const int *diag, const int *upd_ptr, const int *upd, void *vals, void *dinv, int *err) {
+    if (nrows <= 0) return IRK_OK;
+    if (fprec == IRK_FACTOR_FP64) {
+        const size_t smem4 = (size_t)b * b * 8 * 4 + (size_t)b * 8;
+        if (smem4 > 227 * 1024) return IRK_ERR_INVALID;
+        if (smem4 > 48 * 1024)
+            cudaFuncSetAttribute(k_factor_level2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
+        k_factor_level2<double><<<nrows, 256, smem4, st>>>(rows, b, rp, ci, diag, upd_ptr, upd, (double *)vals,
+                                                           (double *)dinv, err);
+    } else {
+        const size_t smem4 = (size_t)b * b * 4 * 4 + (size_t)b * 4;
+        if (smem4 > 227 * 1024) return IRK_ERR_INVALID;
+        if (smem4 > 48 * 1024)
+            cudaFuncSetAttribute(k_factor_level2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
+        k_factor_level2<float><<<nrows, 256, smem4, st>>>(rows, b, rp, ci, diag, upd_ptr, upd, (float *)vals,
+                                                          (float *)dinv, err);
+    }
+    return cuda_status(cudaGetLastError());
+}
+
+template <class AR, class C>
+static int sweep_group_impl(cudaStream_t st, int dev, int nitems, int b, int max_item_blocks, const int *lo,
+                            const int *up, const int *rp, const int *ci, const int *voff, const void *vals,
+                            const void *dinv, vec8 *vpool, unsigned long long *llpool, int ep, int *err,
+                            SweepLanes lanes) {
+    auto kern = k_sweep_staged<AR, C, C>;
+    const int threads = 128, warps = threads / 32;
+    const size_t slot_stride = ((size_t)b * b * sizeof(C) + 127) / 128 * 128;
+    int NS = std::max(1, std::min(std::min(max_item_blocks, 16), (int)((48 * 1024) / slot_stride)));
+    const size_t smem = (slot_stride * NS + 128) * warps;
+    if (smem > 227 * 1024) return IRK_ERR_INVALID;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0, sms = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int grid = per_sm * sms;
+    if (grid <= 0) return IRK_ERR_CUDA;
+    int nb = nitems;
+    const C *vv = (const C *)vals, *dd = (const C *)dinv;
+    const vec8 *v = vpool;
+    vec8 *z = vpool;
+    unsigned long long *yll = llpool, *zll = llpool;
+    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &voff, &vv, &dd, &v, &yll, &zll, &z, &ep, &err, &lanes};
+    return cuda_status(cudaLaunchCooperativeKernel((const void *)kern, grid, threads, args, smem, st));
+}
+
+// Cooperative sweep over a merged work list of several requests: lo / up hold
+// nitems forward / backward rows; per-lane bases in vec8 (vectors) and word
+// (published values) units relative to vpool / llpool.
+int ilu_sweep_group(cudaStream_t st, int dev, int fprec, int df, int nitems, int b, int max_item_blocks,
+                    const int *lo, const int *up, const int *rp, const int *ci, const int *voff, const void *vals,
+                    const void *dinv, vec8 *vpool, unsigned long long *llpool, int ep, int *err,
+                    const int *lane_of_row, const long long *vin, const long long *zout, const long long *yll,
+                    const long long *zll) {
+    SweepLanes L = {lane_of_row, vin, zout, yll, zll};
+    if (df) {
+        if (fprec == IRK_FACTOR_FP64)
+            return sweep_group_impl<ArDF, double>(st, dev, nitems, b, max_item_blocks, lo, up, rp, ci, voff, vals,
+                                                  dinv, vpool, llpool, ep, err, L);
+        return sweep_group_impl<ArDF, float>(st, dev, nitems, b, max_item_blocks, lo, up, rp, ci, voff, vals, dinv,
+                                             vpool, llpool, ep, err, L);
+    }
+    if (fprec == IRK_FACTOR_FP64)
+        return sweep_group_impl<ArF64, double>(st, dev, nitems, b, max_item_blocks, lo, up, rp, ci, voff, vals, dinv,
+                                               vpool, llpool, ep, err, L);
+    return sweep_group_impl<ArF64, float>(st, dev, nitems, b, max_item_blocks, lo, up, rp, ci, voff, vals, dinv,
+                                          vpool, llpool, ep, err, L);
 }

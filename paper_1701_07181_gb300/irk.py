@@ -54,7 +54,9 @@ class Stats(ctypes.Structure):
 
 EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor", "irk_solve",
            "irk_apply_operator", "irk_apply_precond", "irk_get_stats", "irk_destroy",
-           "irk_strerror", "irk_apply_precond_noalloc"]
+           "irk_strerror", "irk_apply_precond_noalloc", "irk_group_create", "irk_group_submit",
+           "irk_group_step", "irk_group_query", "irk_group_collect", "irk_group_device_bytes",
+           "irk_group_destroy"]
 
 
 def load():
@@ -82,6 +84,15 @@ def load():
         lib.irk_strerror.argtypes = [I]
         lib.irk_strerror.restype = ctypes.c_char_p
         lib.irk_apply_precond_noalloc.argtypes = [P, P, P, P]
+        lib.irk_group_create.argtypes = [ctypes.POINTER(P), I, P, I, I, I, I, ctypes.POINTER(Options)]
+        lib.irk_group_submit.argtypes = [P, I, P, P, P, P, P, D, D, I, ctypes.POINTER(I)]
+        lib.irk_group_step.argtypes = [P, ctypes.POINTER(I)]
+        lib.irk_group_query.argtypes = [P, I, ctypes.POINTER(I), ctypes.POINTER(D), ctypes.POINTER(I)]
+        lib.irk_group_collect.argtypes = [P, I, P, I]
+        lib.irk_group_device_bytes.argtypes = [P]
+        lib.irk_group_device_bytes.restype = ctypes.c_longlong
+        lib.irk_group_destroy.argtypes = [P]
+        lib.irk_group_destroy.restype = None
         _lib = lib
         return lib
 
@@ -214,6 +225,112 @@ class Solver:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.irk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Group:
+    """Multi-request engine (irk_group_*): many stage systems of one class
+    (s, m, options) solved together, admitted and collected between steps."""
+
+    def __init__(self, s, m, max_elements, max_blocks, max_requests, A=None, precond="uncoupled",
+                 factor_prec="fp32", krylov="df64", restart=30, max_iter=3000, ordering="natural",
+                 stream=None, shift=None):
+        lib = load()
+        self._lib = lib
+        self.s, self.m = int(s), int(m)
+        opt = Options()
+        lib.irk_default_options(ctypes.byref(opt))
+        opt.restart = int(restart)
+        opt.max_iter = int(max_iter)
+        opt.precond = PRECOND[precond]
+        opt.factor_prec = FACTOR_PREC[factor_prec]
+        opt.krylov_arith = KRYLOV[krylov]
+        opt.ordering = {"natural": 0, "multicolor": 1}[ordering]
+        self._shift = None
+        if shift is not None:
+            self._shift = np.ascontiguousarray(shift, dtype=np.float64)
+            opt.shift = self._shift.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if stream is not None:
+            opt.stream = ctypes.c_void_p(int(stream))
+        Ap = None
+        if A is not None:
+            self._A = np.ascontiguousarray(A, dtype=np.float64)
+            Ap = self._A.ctypes.data_as(ctypes.c_void_p)
+        h = ctypes.c_void_p()
+        rc = lib.irk_group_create(ctypes.byref(h), self.s, Ap, self.m, int(max_elements), int(max_blocks),
+                                  int(max_requests), ctypes.byref(opt))
+        if rc != IRK_OK:
+            raise IrkError(rc, "irk_group_create")
+        self._h = h
+        self._T = {}
+
+    def submit(self, T, row_ptr, col_idx, J, M, R, dt, rtol=1e-8):
+        """Admit one request; returns its slot, or None when the pools are full."""
+        rp, k1, sp = _ptr(row_ptr, np.int32)
+        ci, k2, _ = _ptr(col_idx, np.int32)
+        Jp, k3, _ = _ptr(J, np.float64)
+        Mp, k4, _ = _ptr(M, np.float64)
+        Rp, k5, _ = _ptr(R, np.float64)
+        slot = ctypes.c_int(-1)
+        rc = self._lib.irk_group_submit(self._h, int(T), rp, ci, Jp, Mp, Rp, float(dt), float(rtol), sp,
+                                        ctypes.byref(slot))
+        if rc == -2:
+            return None
+        if rc != IRK_OK:
+            raise IrkError(rc, "irk_group_submit")
+        self._T[slot.value] = int(T)
+        return slot.value
+
+    def step(self):
+        """One FGMRES iteration of every active request; returns how many remain."""
+        n = ctypes.c_int(0)
+        rc = self._lib.irk_group_step(self._h, ctypes.byref(n))
+        if rc != IRK_OK:
+            raise IrkError(rc, "irk_group_step")
+        return n.value
+
+    def query(self, slot):
+        """(running, iters, relres, status)."""
+        it, rr, stt = ctypes.c_int(0), ctypes.c_double(0.0), ctypes.c_int(0)
+        rc = self._lib.irk_group_query(self._h, int(slot), ctypes.byref(it), ctypes.byref(rr), ctypes.byref(stt))
+        if rc < 0:
+            raise IrkError(rc, "irk_group_query")
+        return rc == 1, it.value, rr.value, stt.value
+
+    def collect(self, slot, out=None, device=None):
+        """W of a finished request (numpy, or a CUDA tensor when device is given)."""
+        N = self.s * self._T[slot] * self.m
+        if out is None:
+            if device is not None:
+                import torch
+                out = torch.empty(N, dtype=torch.float64, device=device)
+            else:
+                out = np.empty(N, dtype=np.float64)
+        Wp, keep, sp = _ptr(out, np.float64)
+        rc = self._lib.irk_group_collect(self._h, int(slot), Wp, sp)
+        if rc != IRK_OK:
+            raise IrkError(rc, "irk_group_collect")
+        del self._T[slot]
+        return out
+
+    def device_bytes(self):
+        return int(self._lib.irk_group_device_bytes(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.irk_group_destroy(self._h)
             self._h = None
 
     def __del__(self):
