@@ -100,9 +100,11 @@ enum irk_krylov_arith { IRK_KRYLOV_FP64 = 0, IRK_KRYLOV_DF64 = 1 };
 enum irk_formulation { IRK_TRANSFORMED = 0, IRK_UNTRANSFORMED = 1 };
 
 /* Scheduling of the preconditioner's block triangular sweeps.  AUTO: one
- * persistent launch per application, rows synchronised by per-row flags
- * (block size <= 128), else LEVELS.  LEVELS: one launch per level of the
- * block-triangular dependency graph. */
+ * persistent launch per application, rows synchronised through published
+ * values (block size <= 128), unless the levels are wide (on average >= 4096
+ * block rows per level, e.g. a multicolour order), where one launch per
+ * level is faster.  LEVELS: one launch per level of the block-triangular
+ * dependency graph. */
 enum irk_sweep_mode { IRK_SWEEP_AUTO = 0, IRK_SWEEP_LEVELS = 1 };
 
 /* Elimination order of the element blocks in the ILU(0) factorisation (the
@@ -208,8 +210,9 @@ IRK_API int irk_apply_precond(irk_ctx *ctx, const double *V, double *Z, int mem_
  *     factors, 2 with FP64 factors) plus 256 bytes; a larger system returns
  *     IRK_ERR_SCRATCH_LIMIT (with FP32 factors: up to 2,097,120 unknowns);
  *   - IRK_ERR_STATE if the context is not factored; IRK_ERR_INVALID if it has
- *     no preconditioner, uses per-level sweeps (block size > 128 or
- *     IRK_SWEEP_LEVELS), or belongs to another device than the current one.
+ *     no preconditioner, uses per-level sweeps (block size > 128,
+ *     IRK_SWEEP_LEVELS, or AUTO choosing per-level launches for wide levels),
+ *     or belongs to another device than the current one.
  * Set-up: the first call on a device (with that device current) looks up
  * the array's device address once; make that first call before any stream
  * capture.  The array is shared by every call on a device and keeps the last

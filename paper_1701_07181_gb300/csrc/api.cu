@@ -4,14 +4,19 @@
 // k_krylov.cu.
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "irk_internal.h"
 
+// Map a CUDA runtime status to the library's codes.  With the environment
+// variable IRK_DEBUG set, failures are also reported on stderr by name.
 int cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return IRK_OK;
+    static const bool debug = getenv("IRK_DEBUG") != nullptr;
+    if (debug) fprintf(stderr, "irk: CUDA error %s (%s)\n", cudaGetErrorName(e), cudaGetErrorString(e));
     if (e == cudaErrorMemoryAllocation) return IRK_ERR_NOMEM;
     return IRK_ERR_CUDA;
 }

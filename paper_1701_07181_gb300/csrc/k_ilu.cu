@@ -27,6 +27,31 @@
 
 namespace {
 
+
+// Allow a kernel the device's full opt-in dynamic shared memory, once per
+// kernel.  The attribute is per function and global to the process: setting
+// it to each launch's own size would race between contexts / groups launching
+// the same kernel from different threads with different block sizes.
+int allow_max_smem(const void *func) {
+    static std::mutex mu;
+    static std::vector<const void *> done;
+    std::lock_guard<std::mutex> g(mu);
+    for (const void *f : done)
+        if (f == func) return IRK_OK;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaFuncAttributes fa;
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, func) != cudaSuccess)
+        return IRK_ERR_CUDA;
+    // the dynamic limit excludes the kernel's static shared memory
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    if (cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) != cudaSuccess)
+        return IRK_ERR_CUDA;
+    done.push_back(func);
+    return IRK_OK;
+}
+
 // ---------------------------------------------------------------------------
 // factor-storage loads (binary64, binary32 or bfloat16 storage)
 __device__ __forceinline__ double ldfac(const double *p) { return __ldg(p); }
@@ -475,6 +500,29 @@ __global__ void k_to_bf16(long long n, const C *src, __nv_bfloat16 *dst) {
         dst[e] = __float2bfloat16_rn((float)src[e]);
 }
 
+// sum_c B[c][a] x[c] for a column-major block (thread's row a pre-applied to
+// B): chunks of 8 columns with every load of a chunk issued before its FMAs
+// (two accumulators), so each thread keeps 8 block loads in flight.
+template <class C, class F>
+__device__ __forceinline__ C block_col_dot(const F *B, const C *x, int b) {
+    C s0 = C(0), s1 = C(0);
+    for (int c0 = 0; c0 < b; c0 += 8) {
+        C bv[8], xv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const bool ok = c0 + u < b;
+            bv[u] = ok ? (C)ldfac(B + (long long)(c0 + u) * b) : C(0);
+            xv[u] = ok ? x[c0 + u] : C(0);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; u += 2) {
+            s0 += bv[u] * xv[u];
+            s1 += bv[u + 1] * xv[u + 1];
+        }
+    }
+    return s0 + s1;
+}
+
 // ---------------------------------------------------------------------------
 // Sweeps.  A group of b threads owns one block row; thread a owns row a.
 //   forward (level of the lower DAG):  y_R = v_R - sum_{p lower} L_p y_col
@@ -494,10 +542,7 @@ __global__ void __launch_bounds__(256) k_sweep_fwd(const int *rows, int nrows, i
     for (int p = rp[R]; p < rp[R + 1]; ++p) {
         const int col = ci[p];
         if (col >= R) break;
-        const F *L = vals + (long long)p * bb + a;
-        const C *yc = y + voff[col];
-#pragma unroll 4
-        for (int c = 0; c < b; ++c) acc -= (C)ldfac(L + (long long)c * b) * yc[c];
+        acc -= block_col_dot<C>(vals + (long long)p * bb + a, y + voff[col], b);
     }
     y[voff[R] + a] = acc;
 }
@@ -520,20 +565,13 @@ __global__ void __launch_bounds__(256) k_sweep_bwd(const int *rows, int nrows, i
         for (int p = rp[R + 1] - 1; p >= rp[R]; --p) {
             const int col = ci[p];
             if (col <= R) break;
-            const F *U = vals + (long long)p * bb + a;
-            const C *zc = y + voff[col];
-#pragma unroll 4
-            for (int c = 0; c < b; ++c) acc -= (C)ldfac(U + (long long)c * b) * zc[c];
+            acc -= block_col_dot<C>(vals + (long long)p * bb + a, y + voff[col], b);
         }
         t[g * b + a] = acc;
     }
     __syncthreads();
     if (!active) return;
-    const F *D = dinv + (long long)R * bb + a;
-    const C *tg = t + g * b;
-    C acc = 0;
-#pragma unroll 4
-    for (int c = 0; c < b; ++c) acc += (C)ldfac(D + (long long)c * b) * tg[c];
+    C acc = block_col_dot<C>(dinv + (long long)R * bb + a, t + g * b, b);
     y[voff[R] + a] = acc;
     AR::st(z + voff[R] + a, CT<C>::template to_vec<AR>(acc));
 }
@@ -822,20 +860,39 @@ __global__ void __launch_bounds__(128) k_sweep_staged(int nb, int b, int NS, con
             pending &= ~(1u << s);
             const F *blk = reinterpret_cast<const F *>(base + slot_stride * s);
             const C sign = is_dinv ? C(1) : C(-1);
+            // chunks of 8 columns: the 8 shuffles and 8 x IRK_PB shared loads of a
+            // chunk are issued before its FMAs; two accumulator sets (even / odd
+            // columns) halve the dependent chain
+            C acc2[IRK_PB];
 #pragma unroll
-            for (int uc = 0; uc < IRK_PB; ++uc) {
-                if (32 * uc >= b) break;
-                const int cmax = min(32, b - 32 * uc);
-                for (int l = 0; l < cmax; ++l) {
-                    const C dv = sign * __shfl_sync(FULL, dep[uc], l);
-                    const F *col = blk + (32 * uc + l) * b;
+            for (int u = 0; u < IRK_PB; ++u) acc2[u] = C(0);
+            for (int c0 = 0; c0 < b; c0 += 8) {
+                const int uc = c0 >> 5;
+                const C src = (uc == 0) ? dep[0] : (uc == 1) ? dep[1] : (uc == 2) ? dep[2] : dep[3];
+                C dv[8];
+                F cv[8][IRK_PB];
+#pragma unroll
+                for (int l = 0; l < 8; ++l) dv[l] = sign * __shfl_sync(FULL, src, (c0 + l) & 31);
+#pragma unroll
+                for (int l = 0; l < 8; ++l)
 #pragma unroll
                     for (int u = 0; u < IRK_PB; ++u) {
-                        int a = lane + 32 * u;
-                        if (a < b) acc[u] += (C)col[a] * dv;
+                        const int a = lane + 32 * u;
+                        cv[l][u] = (c0 + l < b && a < b) ? blk[(c0 + l) * b + a] : F(0);
                     }
-                }
+#pragma unroll
+                for (int l = 0; l < 8; ++l)
+#pragma unroll
+                    for (int u = 0; u < IRK_PB; ++u) {
+                        if (c0 + l >= b) continue;
+                        if (l & 1)
+                            acc2[u] += (C)cv[l][u] * dv[l];
+                        else
+                            acc[u] += (C)cv[l][u] * dv[l];
+                    }
             }
+#pragma unroll
+            for (int u = 0; u < IRK_PB; ++u) acc[u] += acc2[u];
             __syncwarp();
             if (kk + NS < nblk) {
                 stage_block<F>(reinterpret_cast<F *>(base + slot_stride * s), block_ptr(kk + NS), blk_bytes, tma,
@@ -1080,7 +1137,12 @@ int pc_build_pattern(irk_ctx *c) {
         if (cudaMalloc(&P.d_dinv16, (long long)P.nb * bb * 2) != cudaSuccess) return IRK_ERR_NOMEM;
     }
     if (cudaMalloc(&P.d_y, (size_t)c->N * cs) != cudaSuccess) return IRK_ERR_NOMEM;
-    P.persistent = (P.b <= 128) && c->opt.sweep != IRK_SWEEP_LEVELS;
+    // AUTO: one persistent launch when the levels are narrow (the sweep is
+    // bound by the chain of levels); per-level launches when each level holds
+    // enough rows to fill the GPU (few levels, e.g. a multicolour order)
+    const int nlev_lo = (int)h.lo_ptr.size() - 1;
+    const bool wide = nlev_lo > 0 && (long long)h.nb >= 4096LL * nlev_lo;
+    P.persistent = (P.b <= 128) && c->opt.sweep != IRK_SWEEP_LEVELS && !wide;
     if (P.persistent) {
         // self-validating words: cs/4 words of 8 bytes per value, epoch 0 = never written
         const size_t words = (size_t)c->N * (cs / 4);
@@ -1145,10 +1207,8 @@ static int factor_impl(irk_ctx *c, double dt) {
     const size_t smem = (size_t)b * b * sizeof(C) * 2 + (size_t)b * sizeof(C);
     const size_t smem4 = (size_t)b * b * sizeof(C) * 4 + (size_t)b * sizeof(C);
     const bool fast = smem4 <= 227 * 1024;
-    if (fast && smem4 > 48 * 1024)
-        cudaFuncSetAttribute(k_factor_level2<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
-    if (!fast && smem > 48 * 1024)
-        cudaFuncSetAttribute(k_factor_level<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem((const void *)k_factor_level2<C>);
+    allow_max_smem((const void *)k_factor_level<C>);
     const int nlev = (int)P.lo_ptr.size() - 1;
     for (int l = 0; l < nlev; ++l) {
         int n = P.lo_ptr[l + 1] - P.lo_ptr[l];
@@ -1183,16 +1243,18 @@ template <class AR, class C, class F>
 static int apply_persistent(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv) {
     PcSystem &P = c->pc;
     auto kern = k_sweep_staged<AR, C, F>;
-    const int threads = 128, warps = threads / 32;
     const size_t blk_bytes = (size_t)P.b * P.b * sizeof(F);
     const size_t slot_stride = (blk_bytes + 127) / 128 * 128;
-    // slots per warp: the longest item, within about 48 KB per warp
+    // slots per warp: the longest item, within about 48 KB per warp; up to 4
+    // warps per CTA, fewer when one slot is large
     int NS = std::max(1, std::min(std::min(P.max_item_blocks, 16), (int)((48 * 1024) / slot_stride)));
     const size_t warp_bytes = slot_stride * NS + 128;
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(227 * 1024) / warp_bytes));
+    const int threads = 32 * warps;
     const size_t smem = warp_bytes * warps;
     if (smem > 227 * 1024) return IRK_ERR_INVALID;
     if (P.coop_blocks == 0 || P.coop_smem != smem) {
-        if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        allow_max_smem((const void *)kern);
         int per_sm = 0, sms = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev);
@@ -1296,15 +1358,15 @@ int na_sweep(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv, u
              unsigned long long *zll, int *err, cudaStream_t st) {
     PcSystem &P = c->pc;
     auto kern = k_sweep_staged<AR, C, F>;
-    const int threads = 128, warps = threads / 32;
     const size_t blk_bytes = (size_t)P.b * P.b * sizeof(F);
     const size_t slot_stride = (blk_bytes + 127) / 128 * 128;
     int NS = std::max(1, std::min(std::min(P.max_item_blocks, 16), (int)((48 * 1024) / slot_stride)));
-    const size_t smem = (slot_stride * NS + 128) * warps;
+    const size_t warp_bytes = slot_stride * NS + 128;
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(227 * 1024) / warp_bytes));
+    const int threads = 32 * warps;
+    const size_t smem = warp_bytes * warps;
     if (smem > 227 * 1024) return IRK_ERR_INVALID;
-    if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return IRK_ERR_CUDA;
+    if (allow_max_smem((const void *)kern)) return IRK_ERR_CUDA;
     int per_sm = 0, sms = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess || per_sm <= 0)
@@ -1409,15 +1471,13 @@ int ilu_factor_level(cudaStream_t st, int fprec, const int *rows, int nrows, int
     if (fprec == IRK_FACTOR_FP64) {
         const size_t smem4 = (size_t)b * b * 8 * 4 + (size_t)b * 8;
         if (smem4 > 227 * 1024) return IRK_ERR_INVALID;
-        if (smem4 > 48 * 1024)
-            cudaFuncSetAttribute(k_factor_level2<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
+        allow_max_smem((const void *)k_factor_level2<double>);
         k_factor_level2<double><<<nrows, 256, smem4, st>>>(rows, b, rp, ci, diag, upd_ptr, upd, (double *)vals,
                                                            (double *)dinv, err);
     } else {
         const size_t smem4 = (size_t)b * b * 4 * 4 + (size_t)b * 4;
         if (smem4 > 227 * 1024) return IRK_ERR_INVALID;
-        if (smem4 > 48 * 1024)
-            cudaFuncSetAttribute(k_factor_level2<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem4);
+        allow_max_smem((const void *)k_factor_level2<float>);
         k_factor_level2<float><<<nrows, 256, smem4, st>>>(rows, b, rp, ci, diag, upd_ptr, upd, (float *)vals,
                                                           (float *)dinv, err);
     }
@@ -1430,12 +1490,14 @@ static int sweep_group_impl(cudaStream_t st, int dev, int nitems, int b, int max
                             const void *dinv, vec8 *vpool, unsigned long long *llpool, int ep, int *err,
                             SweepLanes lanes) {
     auto kern = k_sweep_staged<AR, C, C>;
-    const int threads = 128, warps = threads / 32;
     const size_t slot_stride = ((size_t)b * b * sizeof(C) + 127) / 128 * 128;
     int NS = std::max(1, std::min(std::min(max_item_blocks, 16), (int)((48 * 1024) / slot_stride)));
-    const size_t smem = (slot_stride * NS + 128) * warps;
+    const size_t warp_bytes = slot_stride * NS + 128;
+    const int warps = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(227 * 1024) / warp_bytes));
+    const int threads = 32 * warps;
+    const size_t smem = warp_bytes * warps;
     if (smem > 227 * 1024) return IRK_ERR_INVALID;
-    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    allow_max_smem((const void *)kern);
     int per_sm = 0, sms = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -201,3 +201,54 @@ def block_size(dim: int, p: int) -> int:
     if dim == 2:
         return (p + 1) * (p + 2) // 2 * 4
     return (p + 1) * (p + 2) * (p + 3) // 6 * 5
+
+
+def make_problem_device(nbrs, m, s, dt, sigma, seed, device, name="device", meta=None):
+    """The same block recipe drawn on the GPU (torch's seeded device
+    generator, so the numbers differ from make_problem's numpy stream): for
+    streams of many or large requests whose host generation would dominate.
+    J, M, R are CUDA float64 tensors; the pattern stays in numpy."""
+    import torch
+    row_ptr, col_idx = bsr_pattern(nbrs)
+    T = len(nbrs)
+    nnzb = int(row_ptr[-1])
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    J = torch.randn((nnzb, m, m), generator=gen, device=device, dtype=torch.float64)
+    rows = np.repeat(np.arange(T), np.diff(row_ptr))
+    diag = torch.as_tensor(rows == col_idx, device=device)
+    inv_sqrt_m = 1.0 / math.sqrt(m)
+    scale = torch.where(diag, inv_sqrt_m, 0.25 * inv_sqrt_m).to(torch.float64)
+    J *= scale[:, None, None]
+    eye = torch.eye(m, device=device, dtype=torch.float64)
+    J[diag] -= sigma * eye
+    Q = torch.randn((T, m, m), generator=gen, device=device, dtype=torch.float64)
+    M = torch.matmul(Q.transpose(1, 2), Q) / m + eye
+    R = torch.randn((s * T * m,), generator=gen, device=device, dtype=torch.float64)
+    return StageProblem(name, s, T, m, row_ptr, col_idx, J, M, R, float(dt), float(sigma), seed,
+                        dict(meta or {}))
+
+
+def serving_stream(n, rate, seed, elements=(1000, 40000), degrees=(1, 2, 3), stages=(2, 3),
+                   dims=(2, 3), dt_range=(1e-3, 1.0)):
+    """Poisson stream of stage-solve requests: arrival times (s), and per
+    request (dim, p, m, s, target elements, dt, seed).  dt is log-uniform."""
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, size=n))
+    out = []
+    for k in range(n):
+        dim = int(rng.choice(dims))
+        p = int(rng.choice(degrees))
+        s = int(rng.choice(stages))
+        T = int(rng.integers(elements[0], elements[1] + 1))
+        dt = float(np.exp(rng.uniform(np.log(dt_range[0]), np.log(dt_range[1]))))
+        out.append(dict(arrival=float(t[k]), dim=dim, p=p, m=block_size(dim, p), s=s, elements=T, dt=dt,
+                        seed=int(seed) * 100003 + k))
+    return out
+
+
+def batched_uneven(n, seed, elements=(500, 5000), degrees=(1, 2, 3), stages=(2, 3)):
+    """Independent 2D meshes with uniform element counts, P1..P3 blocks and
+    2 or 3 stages (the batched uneven workload), as request descriptors."""
+    return serving_stream(n, 1.0, seed, elements=elements, degrees=degrees, stages=stages, dims=(2,),
+                          dt_range=(0.1, 0.1))

@@ -229,3 +229,16 @@ def test_precond_before_factor_is_state_error():
         with pytest.raises(irk.IrkError) as e:
             S.apply_precond(dev(P.R))
         assert e.value.code == -7
+
+
+@pytest.mark.parametrize("fprec,krylov", [("fp64", "fp64"), ("fp32", "df64")])
+def test_large_blocks_3d_p3(fprec, krylov):
+    """m = 100 (3D P3 x 5 variables): the factor and sweep kernels fall back to
+    fewer buffers / warps per CTA to fit shared memory."""
+    P = inputs.make_problem(inputs.mesh_3d_periodic(3), 100, 2, 0.1, 6.0, 17)
+    ref = ref_of(P)
+    W_ref = ref.solve(P.R, P.dt, rtol=1e-12)["x"]
+    with solver(P, precond="uncoupled", factor_prec=fprec, krylov=krylov) as S:
+        W, iters, relres, rc = S.solve(dev(P.R), P.dt, rtol=1e-8)
+    assert rc == 0 and relres <= 1e-8
+    assert rel(W, W_ref) <= 1e-6
