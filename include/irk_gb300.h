@@ -285,6 +285,14 @@ typedef struct {
      * last irk_solve, summed over its calls, from CUDA events on the stream */
     double matvec_ms, precond_ms, ortho_ms;
     int n_matvec, n_precond, n_ortho;
+    /* launch variant of the operator product chosen by the autotuner for this
+     * context's (m, s, arithmetic): 0-3 register-streaming kernel (chunk
+     * width 8/4/2 columns, 256/128 threads), 4-6 bulk-copy pipelined kernel
+     * (2 or 3 shared-memory stages, one or two CTAs per SM; where a stage does
+     * not fit or m is odd it runs variant 0's launch); -1 before the first
+     * product.  The environment variable IRK_MATVEC_VARIANT=<0..6>, read when a
+     * context makes its first product, pins the variant.  Every variant gives the same result bit for bit. */
+    int matvec_variant;
 } irk_stats;
 IRK_API int irk_get_stats(const irk_ctx *ctx, irk_stats *out);
 

@@ -397,8 +397,8 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
               cudaMalloc(&c->d_g, sizeof(double) * (R + 1)) == cudaSuccess &&
               cudaMalloc(&c->d_yls, sizeof(double) * R) == cudaSuccess &&
               cudaMalloc(&c->d_scal, IRK_SCAL_SLOTS * IRK_SCAL_BYTES) == cudaSuccess &&
-              cudaMalloc(&c->d_part, sizeof(vec8) * c->red_blocks) == cudaSuccess &&
-              cudaMalloc(&c->d_ticket, sizeof(unsigned int)) == cudaSuccess &&
+              cudaMalloc(&c->d_part, sizeof(vec8) * IRK_PART_SLOTS) == cudaSuccess &&
+              cudaMalloc(&c->d_ticket, 4 * sizeof(unsigned int)) == cudaSuccess &&
               cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess &&
               cudaMallocHost(&c->h_scal, 4 * IRK_SCAL_BYTES) == cudaSuccess;
     if (!ok) {
@@ -406,7 +406,8 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
         free_ctx(c);
         return IRK_ERR_NOMEM;
     }
-    cudaMemsetAsync(c->d_ticket, 0, sizeof(unsigned int), c->stream);
+    c->d_gbar = c->d_ticket + 2;
+    cudaMemsetAsync(c->d_ticket, 0, 4 * sizeof(unsigned int), c->stream);
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     cudaMemsetAsync(c->d_scal, 0, IRK_SCAL_SLOTS * IRK_SCAL_BYTES, c->stream);
     cudaMemsetAsync(c->d_H, 0, sizeof(double) * (R + 1) * R, c->stream);
@@ -496,6 +497,7 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     const long long N = c->N;
     const int Rs = c->opt.restart;
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    cudaMemsetAsync(c->d_gbar, 0, 2 * sizeof(unsigned int), c->stream);
     double *est_h = c->h_scal, *beta_h = c->h_scal + 1, *hn_h = c->h_scal + 2;
     int total = 0, cycles = 0;
     double bnorm = 0.0, beta = 0.0;
@@ -535,13 +537,20 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
             if ((rc = launch_matvec(c, Zj, w, nullptr, dt, 0))) break;
             tmark_end(c, tm, 0);
             tm = tmark_begin(c);
-            for (int i = 0; i <= j && !rc; ++i)
-                rc = launch_axpy_dot_slot(c, w, i > 0 ? c->d_V + (long long)(i - 1) * N : nullptr, 2 + i - 1,
-                                          c->d_V + (long long)i * N, 0, 0, 2 + i, c->d_H + i * Rs + j);
+            rc = launch_arnoldi(c, j, Rs, w);
+            if (rc == IRK_ERR_INVALID) {
+                // no cooperative launch: one launch per Gram-Schmidt step
+                rc = IRK_OK;
+                for (int i = 0; i <= j && !rc; ++i)
+                    rc = launch_axpy_dot_slot(c, w, i > 0 ? c->d_V + (long long)(i - 1) * N : nullptr, 2 + i - 1,
+                                              c->d_V + (long long)i * N, 0, 0, 2 + i, c->d_H + i * Rs + j);
+                if (rc) break;
+                if ((rc = launch_axpy_dot_slot(c, w, Vj, 2 + j, nullptr, 1, 1, 2 + j + 1,
+                                               c->d_H + (j + 1) * Rs + j)))
+                    break;
+                if ((rc = launch_scale_slot(c, w, 2 + j + 1)) || (rc = launch_givens(c, j, Rs))) break;
+            }
             if (rc) break;
-            if ((rc = launch_axpy_dot_slot(c, w, Vj, 2 + j, nullptr, 1, 1, 2 + j + 1, c->d_H + (j + 1) * Rs + j)))
-                break;
-            if ((rc = launch_scale_slot(c, w, 2 + j + 1)) || (rc = launch_givens(c, j, Rs))) break;
             tmark_end(c, tm, 2);
             ++total;
             jl = j;
@@ -583,6 +592,7 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
 int irk_get_stats(const irk_ctx *c, irk_stats *out) {
     if (!c || !out) return IRK_ERR_INVALID;
     *out = c->stats;
+    out->matvec_variant = c->mv_variant;
     return IRK_OK;
 }
 

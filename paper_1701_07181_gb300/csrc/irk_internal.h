@@ -89,10 +89,12 @@ struct irk_ctx {
     double *h_scal = nullptr;  // pinned host mirror of a few scalars
     void *d_part = nullptr;    // per-CTA partial sums of the reductions
     unsigned int *d_ticket = nullptr;
+    unsigned int *d_gbar = nullptr;  // grid-barrier words of k_arnoldi (in d_ticket's allocation)
     int *d_err = nullptr;
     int red_blocks = 0;
     irk_stats stats;
     long long launches = 0;
+    int mv_variant = -1;  // operator-product launch variant (autotuned on first use)
     // phase timing (irk_options.timing): event pool and (kind, start, end) marks
     std::vector<cudaEvent_t> tev;
     std::vector<int> tkind;
@@ -102,6 +104,8 @@ struct irk_ctx {
 // ---- launchers (k_matvec.cu) ----
 // y = B x (mode 0) or y = rhs - B x (mode 1); form: IRK_TRANSFORMED / UNTRANSFORMED
 int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt, int mode);
+// raise a kernel's dynamic shared-memory limit to the device maximum (once)
+int irk_allow_max_smem(const void *func);
 // stage-major binary64 <-> element-interleaved vec8
 int launch_to_internal(irk_ctx *c, const double *src, vec8 *dst);
 int launch_to_external(irk_ctx *c, const vec8 *src, double *dst);
@@ -113,6 +117,8 @@ int launch_convert_blocks(irk_ctx *c, const double *src, vec8 *dst, long long nb
 // 1 = residual estimate, 2 + i = h_{i,j} of the current column, 64 + i = y_i.
 #define IRK_SCAL_SLOTS 128
 #define IRK_SCAL_BYTES 32
+// entries of the per-CTA partial-sum buffer d_part (>= red_blocks)
+#define IRK_PART_SLOTS 4096
 #define IRK_MAX_RESTART 60
 // w <- w - h[hprev_slot] vprev (if vprev), then slot out = <w, v> (self: v = w;
 // take_sqrt: store the square root); H_out (if non-null) receives the value.
@@ -123,6 +129,7 @@ int launch_scale_slot(irk_ctx *c, vec8 *w, int slot);
 // Givens step for column j; writes the residual estimate to slot 1
 int launch_givens(irk_ctx *c, int j, int restart);
 // back-substitution for y (size jl+1) and x += Z y
+int launch_arnoldi(irk_ctx *c, int j, int restart, vec8 *w);
 int launch_lsq_update(irk_ctx *c, int jl, int restart);
 // g = (beta, 0, ..., 0) with beta from slot 0
 int launch_cycle_start(irk_ctx *c, int restart);

@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "arith.cuh"
+#include "tma.cuh"
 
 #define IRK_MAX_GJ 256
 
@@ -302,9 +303,11 @@ __global__ void __launch_bounds__(256) k_factor_level(const int *rows, int b, co
 // finds the pivot; phase 2 performs the row interchange and the scaling of
 // the pivot row together (each thread owns whole columns c != k) and saves
 // the post-interchange pivot column; phase 3 eliminates, writing column k as
-// -f_r / pivot (rows r != k) and 1 / pivot (row k).
+// -f_r / pivot (rows r != k) and 1 / pivot (row k).  A has leading dimension
+// ld (an odd ld = b + 1 keeps the row accesses of phase 2 free of shared-
+// memory bank conflicts); Out is b x b column-major.
 template <class C>
-__device__ bool gauss_jordan3(C *A, C *Out, int b, C *fcol) {
+__device__ bool gauss_jordan3(C *A, C *Out, int b, C *fcol, int ld) {
     __shared__ int s_piv[IRK_MAX_GJ];
     __shared__ C s_pinv;
     __shared__ int s_bad;
@@ -317,7 +320,7 @@ __device__ bool gauss_jordan3(C *A, C *Out, int b, C *fcol) {
             C best = -1;
             int bi = k;
             for (int rr = k + threadIdx.x; rr < b; rr += 32) {
-                C v = fabs(A[k * b + rr]);
+                C v = fabs(A[k * ld + rr]);
                 if (v > best) {
                     best = v;
                     bi = rr;
@@ -333,7 +336,7 @@ __device__ bool gauss_jordan3(C *A, C *Out, int b, C *fcol) {
             }
             if (threadIdx.x == 0) {
                 s_piv[k] = bi;
-                C pv = A[k * b + bi];
+                C pv = A[k * ld + bi];
                 if (!(best > C(0))) {
                     s_bad = 1;
                     pv = C(1);
@@ -349,13 +352,13 @@ __device__ bool gauss_jordan3(C *A, C *Out, int b, C *fcol) {
                 // column save (post-interchange view of column k)
                 const int rr = t;
                 const int src = (rr == k) ? p : (rr == p ? k : rr);
-                fcol[rr] = A[k * b + src];
+                fcol[rr] = A[k * ld + src];
             } else {
                 const int cc = t - b;
                 if (cc == k) continue;
-                const C ak = A[cc * b + k], ap = A[cc * b + p];
-                A[cc * b + k] = ap * pinv;
-                if (p != k) A[cc * b + p] = ak;
+                const C ak = A[cc * ld + k], ap = A[cc * ld + p];
+                A[cc * ld + k] = ap * pinv;
+                if (p != k) A[cc * ld + p] = ak;
             }
         }
         __syncthreads();
@@ -363,9 +366,9 @@ __device__ bool gauss_jordan3(C *A, C *Out, int b, C *fcol) {
             if (r != k) {
                 const C f = fcol[r];
                 for (int cc = g; cc < b; cc += G)
-                    A[cc * b + r] = (cc == k) ? -f * pinv : A[cc * b + r] - f * A[cc * b + k];
+                    A[cc * ld + r] = (cc == k) ? -f * pinv : A[cc * ld + r] - f * A[cc * ld + k];
             } else if (g == 0) {
-                A[k * b + k] = pinv;
+                A[k * ld + k] = pinv;
             }
         }
         __syncthreads();
@@ -383,7 +386,7 @@ __device__ bool gauss_jordan3(C *A, C *Out, int b, C *fcol) {
     __syncthreads();
     for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
         int j = e / b, rr = e - j * b;
-        Out[e] = A[s_idx[j] * b + rr];
+        Out[e] = A[s_idx[j] * ld + rr];
     }
     __syncthreads();
     return s_bad == 0;
@@ -432,6 +435,92 @@ __device__ __forceinline__ void tile_gemm(C *dst1, C *dst2, const C *X, const C 
     }
 }
 
+// Tensor-core block product for FP32 factors: P = X Y (column-major b x b in
+// shared memory) with mma.sync m16n8k8 on TF32 operands, each operand split
+// into a TF32 head and a TF32 tail so that P = Xh Yh + Xh Yt + Xt Yh keeps
+// about FP32 accuracy (the "3xTF32" scheme).  Dimensions are padded with zeros
+// to multiples of 16 (rows) and 8 (columns, inner).  Fragment layout of the
+// m16n8k8 .tf32 shape (PTX ISA): with g = lane / 4, t = lane % 4,
+//   A: a0 (g, t), a1 (g+8, t), a2 (g, t+4), a3 (g+8, t+4)
+//   B: b0 (t, g), b1 (t+4, g)
+//   C: c0 (g, 2t), c1 (g, 2t+1), c2 (g+8, 2t), c3 (g+8, 2t+1).
+// mode 0: dst1 = P (dst2 too when non-null); mode 1: dst1 -= P.
+__device__ __forceinline__ unsigned to_tf32(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ void tc_gemm(float *dst1, float *dst2, const float *X, const float *Y, int b, int mode) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int mt = (b + 15) / 16, nt = (b + 7) / 8, kt = (b + 7) / 8;
+    for (int tile = warp; tile < mt * nt; tile += nwarps) {
+        const int r0 = (tile % mt) * 16, c0 = (tile / mt) * 8;
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int kk = 0; kk < kt; ++kk) {
+            const int k0 = kk * 8;
+            float av[4], bv[2];
+            const int ar[4] = {r0 + g, r0 + g + 8, r0 + g, r0 + g + 8};
+            const int ak[4] = {k0 + t, k0 + t, k0 + t + 4, k0 + t + 4};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) av[q] = (ar[q] < b && ak[q] < b) ? X[ak[q] * b + ar[q]] : 0.f;
+            const int bk[2] = {k0 + t, k0 + t + 4};
+            const int bc = c0 + g;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) bv[q] = (bk[q] < b && bc < b) ? Y[bc * b + bk[q]] : 0.f;
+            unsigned ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                ah[q] = to_tf32(av[q]);
+                al[q] = to_tf32(av[q] - __uint_as_float(ah[q]));
+            }
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                bh[q] = to_tf32(bv[q]);
+                bl[q] = to_tf32(bv[q] - __uint_as_float(bh[q]));
+            }
+            mma_tf32(d, al, bh);  // small terms first
+            mma_tf32(d, ah, bl);
+            mma_tf32(d, ah, bh);
+        }
+        const int rr[4] = {r0 + g, r0 + g, r0 + g + 8, r0 + g + 8};
+        const int cc[4] = {c0 + 2 * t, c0 + 2 * t + 1, c0 + 2 * t, c0 + 2 * t + 1};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            if (rr[q] >= b || cc[q] >= b) continue;
+            const int e = cc[q] * b + rr[q];
+            if (mode == 0) {
+                dst1[e] = d[q];
+                if (dst2) dst2[e] = d[q];
+            } else {
+                dst1[e] -= d[q];
+            }
+        }
+    }
+}
+
+template <class C>
+__device__ __forceinline__ void block_product(C *dst1, C *dst2, const C *X, const C *Y, int b, int mode);
+template <>
+__device__ __forceinline__ void block_product<float>(float *dst1, float *dst2, const float *X, const float *Y, int b,
+                                                     int mode) {
+    tc_gemm(dst1, dst2, X, Y, b, mode);
+}
+template <>
+__device__ __forceinline__ void block_product<double>(double *dst1, double *dst2, const double *X, const double *Y,
+                                                      int b, int mode) {
+    tile_gemm<double>(dst1, dst2, X, Y, b, mode);
+}
+
 // Load two b x b blocks from global memory into shared memory with every
 // thread's loads issued before its stores (one memory round trip).
 template <class C>
@@ -464,8 +553,8 @@ __global__ void __launch_bounds__(256) k_factor_level2(const int *rows, int b, c
                                                        C *vals, C *dinv, int *err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int bb = b * b;
-    C *X = reinterpret_cast<C *>(smem_raw);
-    C *Y = X + bb;
+    C *X = reinterpret_cast<C *>(smem_raw);  // b * (b + 1): also the padded copy for Gauss-Jordan
+    C *Y = X + bb + b;
     C *L = Y + bb;
     C *D = L + bb;
     C *fcol = D + bb;
@@ -477,19 +566,24 @@ __global__ void __launch_bounds__(256) k_factor_level2(const int *rows, int b, c
         if (i >= R) break;
         load_pair<C>(X, vals + (long long)p * bb, Y, dinv + (long long)i * bb, bb);
         __syncthreads();
-        tile_gemm<C>(L, vals + (long long)p * bb, X, Y, b, 0);  // L_p = B_p D_i^{-1}
+        block_product<C>(L, vals + (long long)p * bb, X, Y, b, 0);  // L_p = B_p D_i^{-1}
         __syncthreads();
         for (int u = upd_ptr[p]; u < upd_ptr[p + 1]; ++u) {
             const int q = upd[2 * u], pos = upd[2 * u + 1];
             load_pair<C>(X, vals + (long long)pos * bb, nullptr, nullptr, bb);
             __syncthreads();
-            tile_gemm<C>((q == dpos) ? D : vals + (long long)q * bb, nullptr, L, X, b, 1);  // B_q -= L_p B_pos
+            block_product<C>((q == dpos) ? D : vals + (long long)q * bb, nullptr, L, X, b, 1);  // B_q -= L_p B_pos
             __syncthreads();
         }
     }
-    for (int e = threadIdx.x; e < bb; e += blockDim.x) vals[(long long)dpos * bb + e] = D[e];
+    // D to global (the U~ diagonal block) and to X with leading dimension b + 1
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) {
+        const int col = e / b, row = e - col * b;
+        vals[(long long)dpos * bb + e] = D[e];
+        X[col * (b + 1) + row] = D[e];
+    }
     __syncthreads();
-    bool ok = gauss_jordan3(D, Y, b, fcol);
+    const bool ok = gauss_jordan3(X, Y, b, fcol, b + 1);
     for (int e = threadIdx.x; e < bb; e += blockDim.x) dinv[(long long)R * bb + e] = Y[e];
     if (!ok && threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_SINGULAR);
 }
@@ -586,7 +680,6 @@ __global__ void __launch_bounds__(256) k_sweep_bwd(const int *rows, int nrows, i
 // list, so the lowest unfinished item can always proceed.  Waits are bounded:
 // after IRK_SPIN_LIMIT polls, or as soon as another warp reported a timeout,
 // the warp records IRK_DEV_ERR_TIMEOUT and leaves.
-#define IRK_SPIN_LIMIT (1 << 20)
 #define IRK_PB 4  // values per lane: b <= 128
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -620,40 +713,9 @@ __device__ __forceinline__ bool wait_epoch(const int *flag, int ep, int *err) {
 __device__ __forceinline__ float ldcg_c(const float *p) { return __ldcg(p); }
 __device__ __forceinline__ double ldcg_c(const double *p) { return __ldcg(p); }
 
-// Shared-memory staging of factor blocks: cp.async.bulk (TMA bulk copy)
-// completing on an mbarrier; plain loads when the block is not 16-byte
-// aligned / sized.
-__device__ __forceinline__ unsigned smem_u32(const void *p) {
-    return (unsigned)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(unsigned long long *bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_arrive(unsigned long long *bar, unsigned bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void tma_load_1d(void *dst, const void *src, unsigned bytes, unsigned long long *bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-// bounded wait for the given phase parity; false after the limit
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
-    for (int spins = 0; spins < IRK_SPIN_LIMIT; ++spins) {
-        unsigned ok;
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ok)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (ok) return true;
-    }
-    return false;
-}
-
+// Shared-memory staging of factor blocks: cp.async.bulk (TMA bulk copy, the
+// helpers of tma.cuh) completing on an mbarrier; plain loads when the block is
+// not 16-byte aligned / sized.
 // Stage one block (nbytes, element type F) into a slot: TMA when possible.
 template <class F>
 __device__ __forceinline__ void stage_block(F *slot, const F *src, unsigned nbytes, bool tma,
@@ -1002,6 +1064,9 @@ size_t csize(int fprec) { return fprec == IRK_FACTOR_FP64 ? 8 : 4; }
 
 }  // namespace
 
+// exported to the other translation units (operator product)
+int irk_allow_max_smem(const void *func) { return allow_max_smem(func); }
+
 // Build the block pattern of the matrix to factor for the context's
 // preconditioner kind (see the file comment), its level schedules and the
 // update lists of the IKJ factorisation, and allocate the factor storage.
@@ -1205,7 +1270,7 @@ static int factor_impl(irk_ctx *c, double dt) {
     c->launches++;
     const int b = P.b;
     const size_t smem = (size_t)b * b * sizeof(C) * 2 + (size_t)b * sizeof(C);
-    const size_t smem4 = (size_t)b * b * sizeof(C) * 4 + (size_t)b * sizeof(C);
+    const size_t smem4 = (size_t)b * b * sizeof(C) * 4 + (size_t)2 * b * sizeof(C);
     const bool fast = smem4 <= 227 * 1024;
     allow_max_smem((const void *)k_factor_level2<C>);
     allow_max_smem((const void *)k_factor_level<C>);
@@ -1469,13 +1534,13 @@ int ilu_factor_level(cudaStream_t st, int fprec, const int *rows, int nrows, int
                      const int *diag, const int *upd_ptr, const int *upd, void *vals, void *dinv, int *err) {
     if (nrows <= 0) return IRK_OK;
     if (fprec == IRK_FACTOR_FP64) {
-        const size_t smem4 = (size_t)b * b * 8 * 4 + (size_t)b * 8;
+        const size_t smem4 = (size_t)b * b * 8 * 4 + (size_t)2 * b * 8;
         if (smem4 > 227 * 1024) return IRK_ERR_INVALID;
         allow_max_smem((const void *)k_factor_level2<double>);
         k_factor_level2<double><<<nrows, 256, smem4, st>>>(rows, b, rp, ci, diag, upd_ptr, upd, (double *)vals,
                                                            (double *)dinv, err);
     } else {
-        const size_t smem4 = (size_t)b * b * 4 * 4 + (size_t)b * 4;
+        const size_t smem4 = (size_t)b * b * 4 * 4 + (size_t)2 * b * 4;
         if (smem4 > 227 * 1024) return IRK_ERR_INVALID;
         allow_max_smem((const void *)k_factor_level2<float>);
         k_factor_level2<float><<<nrows, 256, smem4, st>>>(rows, b, rp, ci, diag, upd_ptr, upd, (float *)vals,

@@ -6,6 +6,9 @@
 // order of work, and the last CTA to finish (ticket counter) sums the
 // partials in index order with a fixed tree.  No floating-point atomics, so
 // the same input gives bit-identical results.
+#include <algorithm>
+#include <mutex>
+
 #include "arith.cuh"
 
 namespace {
@@ -113,10 +116,9 @@ __global__ void k_scale_inv(long long N, vec8 *w, const Scal *h) {
         AR::st(w + e, AR::mul(AR::ld(w + e), inv));
 }
 
-// Givens rotations on column j of H (binary64, one thread).
-__global__ void k_givens(int j, int R, double *H, double *cs, double *sn, double *g, double *est,
-                         int *err) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Givens rotations on column j of H (binary64, one thread): the earlier
+// rotations, then the new one that zeroes H[j+1][j]; est = |g[j+1]|.
+__device__ void givens_col(int j, int R, double *H, double *cs, double *sn, double *g, double *est, int *err) {
     for (int i = 0; i < j; ++i) {
         double a = H[i * R + j], b = H[(i + 1) * R + j];
         H[i * R + j] = cs[i] * a + sn[i] * b;
@@ -138,6 +140,136 @@ __global__ void k_givens(int j, int R, double *H, double *cs, double *sn, double
     g[j + 1] = -s * g[j];
     g[j] = c * g[j];
     *est = fabs(g[j + 1]);
+}
+
+__global__ void k_givens(int j, int R, double *H, double *cs, double *sn, double *g, double *est,
+                         int *err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    givens_col(j, R, H, cs, sn, g, est, err);
+}
+
+// Bounded grid-wide barrier of a cooperative launch (every CTA resident):
+// bar[0] counts the arrivals of the current generation, bar[1] is the
+// generation.  After IRK_SPIN_LIMIT polls a CTA records a timeout and the
+// barrier returns false (the caller leaves; the host resets bar per solve).
+#define IRK_GRID_SPIN_LIMIT (1 << 20)
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ bool grid_sync(unsigned *bar, int *err, int *s_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = ld_acquire_u32(bar + 1);
+        __threadfence();
+        if (atomicAdd(bar, 1u) == gridDim.x - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            int spins = 0;
+            while (ld_acquire_u32(bar + 1) == gen) {
+                if (++spins > IRK_GRID_SPIN_LIMIT) {
+                    ok = 0;
+                    atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *s_ok = ok;
+    }
+    __syncthreads();
+    return *s_ok != 0;
+}
+
+// One Arnoldi step of FGMRES after the operator product w = B z_j, in one
+// cooperative launch: modified Gram-Schmidt against v_0..v_j (for i = 0..j:
+// w -= h_{i-1,j} v_{i-1}, fused with h_{i,j} = <w, v_i>), then
+// w -= h_{j,j} v_j with h_{j+1,j} = ||w||, w /= h_{j+1,j} (zero on
+// breakdown), and the Givens rotations of column j.  The same element
+// operations and scalar splits as k_axpy_dot / k_scale_inv; each reduction's
+// per-CTA partials are summed in index order by every CTA (identical values
+// everywhere, deterministic), in a buffer alternating between steps so that a
+// CTA already in the next step never overwrites partials still being read.
+template <class AR>
+__global__ void __launch_bounds__(256) k_arnoldi(long long N, int j, int R, vec8 *w, const vec8 *V, Scal *slots,
+                                                 double *H, double *cs, double *sn, double *g, double *est,
+                                                 vec8 *part, unsigned *bar, int *err) {
+    typedef typename AR::val val;
+    __shared__ val sh[32];
+    __shared__ int s_ok;
+    __shared__ double s_h;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double hprev = 0.0;
+    for (int i = 0; i <= j + 1; ++i) {
+        const bool last = i == j + 1;
+        const vec8 *vp = i > 0 ? V + (long long)(i - 1) * N : nullptr;
+        const vec8 *vi = last ? nullptr : V + (long long)i * N;
+        const float hh = (float)hprev;
+        const val nh = AR::neg(AR::coef(hprev, hh, (float)(hprev - (double)hh)));
+        typename AR::acc acc = AR::zero();
+        // U elements per thread and round, all loads issued before the
+        // arithmetic; accumulation in the thread's element order
+        constexpr int U = 4;
+        for (long long e = e0; e < N; e += U * stride) {
+            val wv[U], pv[U], xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long ee = e + u * stride;
+                const bool ok = ee < N;
+                wv[u] = ok ? AR::ldcg(w + ee) : AR::from_float(0.f);  // written by this thread in the previous step
+                pv[u] = (ok && vp) ? AR::ld(vp + ee) : AR::from_float(0.f);
+                xv[u] = (ok && !last) ? AR::ld(vi + ee) : AR::from_float(0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const long long ee = e + u * stride;
+                if (ee >= N) break;
+                if (vp) {
+                    wv[u] = AR::add(wv[u], AR::mul(nh, pv[u]));
+                    AR::st(w + ee, wv[u]);
+                }
+                AR::fma(acc, wv[u], last ? wv[u] : xv[u]);
+            }
+        }
+        vec8 *pb = part + (i & 1) * gridDim.x;
+        const val r = block_reduce<AR>(AR::value(acc), sh);
+        if (threadIdx.x == 0) AR::st(pb + blockIdx.x, r);
+        if (!grid_sync(bar, err, &s_ok)) return;
+        typename AR::acc a2 = AR::zero();
+        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) AR::add_to(a2, AR::ldcg(pb + q));
+        const val tot = block_reduce<AR>(AR::value(a2), sh);
+        if (threadIdx.x == 0) {
+            double d = AR::to_double(tot);
+            if (!isfinite(d)) {
+                if (blockIdx.x == 0) atomicOr(err, IRK_DEV_ERR_NONFINITE);
+                d = 0.0;
+            }
+            if (last) d = d > 0.0 ? sqrt(d) : 0.0;
+            s_h = d;
+            if (blockIdx.x == 0) {
+                scal_store_d(slots + 2 + i, d);
+                H[i * R + j] = d;
+            }
+        }
+        __syncthreads();
+        hprev = s_h;
+    }
+    const double inv = hprev != 0.0 ? 1.0 / hprev : 0.0;
+    const float ih = (float)inv;
+    const val iv = AR::coef(inv, ih, (float)(inv - (double)ih));
+    for (long long e = e0; e < N; e += 2 * stride) {
+        const long long e2 = e + stride;
+        const val a0 = AR::ldcg(w + e);
+        const val a1 = e2 < N ? AR::ldcg(w + e2) : AR::from_float(0.f);
+        AR::st(w + e, AR::mul(a0, iv));
+        if (e2 < N) AR::st(w + e2, AR::mul(a1, iv));
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) givens_col(j, R, H, cs, sn, g, est, err);
 }
 
 // y = H(0:jl, 0:jl)^{-1} g(0:jl) (one thread), stored as Scal for the update.
@@ -221,6 +353,52 @@ int launch_givens(irk_ctx *c, int j, int restart) {
     k_givens<<<1, 32, 0, c->stream>>>(j, restart, c->d_H, c->d_cs, c->d_sn, c->d_g, &scal(c, 1)->d, c->d_err);
     c->launches++;
     return cuda_status(cudaGetLastError());
+}
+
+// Grid of k_arnoldi: every CTA resident (cooperative launch), as many as fit
+// (streaming needs the loads of every resident thread in flight), at most
+// half of IRK_PART_SLOTS (the partial buffer holds two steps); 0 when the
+// device has no cooperative launch.
+static int arnoldi_grid(irk_ctx *c) {
+    static std::mutex mu;
+    static int cached[2] = {-1, -1};
+    std::lock_guard<std::mutex> lk(mu);
+    int &gsz = cached[c->df ? 1 : 0];
+    if (gsz < 0) {
+        int dev = 0, coop = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (c->df)
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<ArDF>, 256, 0);
+        else
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<ArF64>, 256, 0);
+        gsz = coop ? sms * per_sm : 0;
+    }
+    return std::min(gsz, IRK_PART_SLOTS / 2);
+}
+
+// The whole Arnoldi step j (orthogonalisation, normalisation, Givens) in one
+// launch; returns IRK_ERR_INVALID when the device cannot launch it (the
+// caller then issues the step as separate launches).
+int launch_arnoldi(irk_ctx *c, int j, int restart, vec8 *w) {
+    const int grid = arnoldi_grid(c);
+    if (grid <= 0) return IRK_ERR_INVALID;
+    long long N = c->N;
+    int jj = j, R = restart;
+    const vec8 *V = c->d_V;
+    Scal *slots = scal(c, 0);
+    double *est = &scal(c, 1)->d;
+    vec8 *part = reinterpret_cast<vec8 *>(c->d_part);
+    void *args[] = {&N, &jj, &R, &w, &V, &slots, &c->d_H, &c->d_cs, &c->d_sn, &c->d_g, &est, &part, &c->d_gbar,
+                    &c->d_err};
+    cudaError_t e;
+    if (c->df)
+        e = cudaLaunchCooperativeKernel((const void *)k_arnoldi<ArDF>, grid, 256, args, 0, c->stream);
+    else
+        e = cudaLaunchCooperativeKernel((const void *)k_arnoldi<ArF64>, grid, 256, args, 0, c->stream);
+    c->launches++;
+    return cuda_status(e);
 }
 
 int launch_lsq_update(irk_ctx *c, int jl, int restart) {

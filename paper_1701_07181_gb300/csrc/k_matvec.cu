@@ -16,7 +16,14 @@
 // stage vectors of the neighbour j (element-interleaved, s*m contiguous
 // values) are read by all m threads of the group at the same address
 // (a broadcast through L1).
+#include <stdlib.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+
 #include "arith.cuh"
+#include "tma.cuh"
 
 namespace {
 
@@ -50,6 +57,50 @@ __device__ __forceinline__ void accum_block(typename AR::acc (&dst)[S], const ve
     }
 }
 
+// Mixes the per-stage sums of row i (t_l = sum_j J_ij x_{l,j},
+// z_l = M_i x_{l,i}) into the s outputs of thread row a and stores them
+// (mode 1: rhs - y).
+template <class AR, int S>
+__device__ __forceinline__ void store_row(const MatvecParams &P, long long i, int a, const typename AR::acc (&t)[S],
+                                          const typename AR::acc (&z)[S]) {
+    typedef typename AR::val val;
+    typedef typename AR::acc acc;
+    const int m = P.m;
+    const long long sm = (long long)S * m;
+    val tv[S], zv[S];
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+        tv[l] = AR::value(t[l]);
+        zv[l] = AR::value(z[l]);
+    }
+    const val mdt = AR::coef(P.mdt.d, P.mdt.hi, P.mdt.lo);
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        acc o = AR::zero();
+        if (P.form == IRK_TRANSFORMED) {
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+                const KCoef &cc = P.C[k * S + l];
+                AR::fma(o, AR::coef(cc.d, cc.hi, cc.lo), zv[l]);
+            }
+            AR::fma(o, mdt, tv[k]);
+        } else {
+            AR::add_to(o, zv[k]);
+            acc q = AR::zero();
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+                const KCoef &cc = P.C[k * S + l];
+                AR::fma(q, AR::coef(cc.d, cc.hi, cc.lo), tv[l]);
+            }
+            AR::fma(o, mdt, AR::value(q));
+        }
+        val out = AR::value(o);
+        vec8 *dst = P.y + i * sm + k * m + a;
+        if (P.mode == 1) out = AR::sub(AR::ld(P.rhs + i * sm + k * m + a), out);
+        AR::st(dst, out);
+    }
+}
+
 template <class AR, int S, int CH>
 __global__ void __launch_bounds__(256) k_matvec(MatvecParams P) {
     typedef typename AR::val val;
@@ -72,39 +123,201 @@ __global__ void __launch_bounds__(256) k_matvec(MatvecParams P) {
         for (int p = p0; p < p1; ++p)
             accum_block<AR, S, CH>(t, P.J + (long long)p * mm + a, P.x + (long long)P.ci[p] * sm, m);
         accum_block<AR, S, CH>(z, P.M + i * mm + a, P.x + i * sm, m);
-        val tv[S], zv[S];
+        store_row<AR, S>(P, i, a, t, z);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined variant.  A CTA owns G element rows at a time (G groups of m
+// threads, as above) and streams, for every group, the next block of its row
+// (J_ij for the row's neighbours in column order, then M_i) together with
+// the s*m stage values that block multiplies through a ring of NS shared-
+// memory stages.  One thread issues the bulk copies (cp.async.bulk completing
+// on the stage's mbarrier) NS stages ahead; the other threads only compute
+// from shared memory, so every SM keeps NS-1 stages (tens of KB) of HBM reads
+// in flight independently of its register-limited occupancy.  The
+// accumulation order is the same as k_matvec's (blocks in column order,
+// columns ascending), so both variants give bitwise identical results.
+template <class AR>
+__device__ __forceinline__ typename AR::val lds(const vec8 *p);
+template <>
+__device__ __forceinline__ double lds<ArF64>(const vec8 *p) {
+    return *reinterpret_cast<const double *>(p);
+}
+template <>
+__device__ __forceinline__ df64 lds<ArDF>(const vec8 *p) {
+    const float2 f = *reinterpret_cast<const float2 *>(p);
+    return df_make(f.x, f.y);
+}
+
+// dst[l] += sum_c B[c*m] x[l*m + c] (B and x in shared memory; B already
+// offset by the thread's row), columns in ascending order.
+template <class AR, int S>
+__device__ __forceinline__ void accum_block_smem(typename AR::acc (&dst)[S], const vec8 *B, const vec8 *x, int m) {
+    typedef typename AR::val val;
+    constexpr int U = 4;
+    int c = 0;
+    for (; c + U <= m; c += U) {
+        val bv[U], xv[S][U];
 #pragma unroll
-        for (int l = 0; l < S; ++l) {
-            tv[l] = AR::value(t[l]);
-            zv[l] = AR::value(z[l]);
-        }
-        const val mdt = AR::coef(P.mdt.d, P.mdt.hi, P.mdt.lo);
+        for (int u = 0; u < U; ++u) bv[u] = lds<AR>(B + (c + u) * m);
 #pragma unroll
-        for (int k = 0; k < S; ++k) {
-            acc o = AR::zero();
-            if (P.form == IRK_TRANSFORMED) {
+        for (int l = 0; l < S; ++l)
 #pragma unroll
-                for (int l = 0; l < S; ++l) {
-                    const KCoef &cc = P.C[k * S + l];
-                    AR::fma(o, AR::coef(cc.d, cc.hi, cc.lo), zv[l]);
-                }
-                AR::fma(o, mdt, tv[k]);
-            } else {
-                AR::add_to(o, zv[k]);
-                acc q = AR::zero();
+            for (int u = 0; u < U; ++u) xv[l][u] = lds<AR>(x + l * m + c + u);
 #pragma unroll
-                for (int l = 0; l < S; ++l) {
-                    const KCoef &cc = P.C[k * S + l];
-                    AR::fma(q, AR::coef(cc.d, cc.hi, cc.lo), tv[l]);
-                }
-                AR::fma(o, mdt, AR::value(q));
-            }
-            val out = AR::value(o);
-            vec8 *dst = P.y + i * sm + k * m + a;
-            if (P.mode == 1) out = AR::sub(AR::ld(P.rhs + i * sm + k * m + a), out);
-            AR::st(dst, out);
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int l = 0; l < S; ++l) AR::fma(dst[l], bv[u], xv[l][u]);
+    }
+    for (; c < m; ++c) {
+        const val b = lds<AR>(B + c * m);
+#pragma unroll
+        for (int l = 0; l < S; ++l) AR::fma(dst[l], b, lds<AR>(x + l * m + c));
+    }
+}
+
+#define IRK_MV_MAX_STAGES 4
+#define IRK_MV_HEADER 256  // bytes before the slots: barriers, timeout words, producer cursors
+
+// Shared-memory bytes of the pipelined variant with G groups and NS stages.
+inline size_t mv_pipe_smem(int m, int s, int G, int NS) {
+    return IRK_MV_HEADER + (size_t)NS * G * ((size_t)m * m + (size_t)s * m) * sizeof(vec8);
+}
+
+template <class AR, int S>
+__global__ void __launch_bounds__(256) k_matvec_pipe(MatvecParams P, int G, int NS, int *err) {
+    typedef typename AR::acc acc;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem_raw);  // NS barriers, G arrivals each
+    int *s_to = reinterpret_cast<int *>(smem_raw + 64);                           // timeout words, by parity
+    vec8 *slots = reinterpret_cast<vec8 *>(smem_raw + IRK_MV_HEADER);
+    const int m = P.m;
+    const int mm = m * m, sm = S * m, slot = mm + sm;
+    const int g = threadIdx.x / m, a = threadIdx.x - g * m;
+    const bool member = g < G;
+    const long long T = P.T;
+    // row that group gg handles in its sweep tt
+#define MV_ROW(gg, tt) (((long long)blockIdx.x + (long long)(tt) * gridDim.x) * G + (gg))
+
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NS; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bars + q)), "r"(G) : "memory");
+        s_to[0] = s_to[1] = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // Producer lanes: thread gg < G issues the copies of group gg, one block
+    // per stage, and arrives on the stage's barrier (with the bytes it
+    // expects, or plainly once its rows are done), so every stage completes
+    // after G arrivals.  The next block's addresses are computed right after
+    // an issue, a whole stage before they are needed: the dependent index
+    // loads (rp, ci) stay off the critical path.
+    const bool producer = threadIdx.x < G;
+    long long pt = 0, pi = T;
+    int pp = 0, pp1 = 0;
+    const vec8 *psrc = nullptr, *pxs = nullptr;
+    int issued = 0;
+    if (producer) {
+        pi = MV_ROW(threadIdx.x, 0);
+        if (pi < T) {
+            pp = P.rp[pi];
+            pp1 = P.rp[pi + 1];
+            psrc = pp < pp1 ? P.J + (long long)pp * mm : P.M + pi * mm;
+            pxs = P.x + (pp < pp1 ? (long long)P.ci[pp] : pi) * sm;
         }
     }
+    auto issue = [&](int q) {
+        unsigned long long *bar = bars + q;
+        if (pi < T) {
+            vec8 *dst = slots + ((long long)q * G + threadIdx.x) * slot;
+            mbar_expect_arrive(bar, (unsigned)slot * (unsigned)sizeof(vec8));
+            tma_load_1d(dst, psrc, (unsigned)mm * sizeof(vec8), bar);
+            tma_load_1d(dst + mm, pxs, (unsigned)sm * sizeof(vec8), bar);
+            if (pp < pp1) {
+                ++pp;
+            } else {
+                pi = MV_ROW(threadIdx.x, ++pt);
+                if (pi < T) {
+                    pp = P.rp[pi];
+                    pp1 = P.rp[pi + 1];
+                }
+            }
+            if (pi < T) {
+                psrc = pp < pp1 ? P.J + (long long)pp * mm : P.M + pi * mm;
+                pxs = P.x + (pp < pp1 ? (long long)P.ci[pp] : pi) * sm;
+            }
+        } else {
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+        }
+        ++issued;
+    };
+    if (producer) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (int q = 0; q < NS; ++q) issue(q);
+    }
+
+    // Consumer: the same block sequence for this thread's group.
+    long long tsw = 0;
+    long long i = member ? MV_ROW(g, 0) : T;
+    int p = 0, p1 = 0;
+    if (i < T) {
+        p = P.rp[i];
+        p1 = P.rp[i + 1];
+    }
+    bool have = i < T;
+    acc t[S], z[S];
+#pragma unroll
+    for (int l = 0; l < S; ++l) {
+        t[l] = AR::zero();
+        z[l] = AR::zero();
+    }
+    int k = 0;
+    for (;; ++k) {
+        // every thread is done with stage k-1 here: its slot may be refilled
+        const int more = __syncthreads_or(have);
+        if (s_to[(k + 1) & 1] || !more) break;  // block-uniform
+        if (producer && k > 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            issue((k - 1) % NS);
+        }
+        if (!have) continue;
+        const int q = k % NS;
+        if (!mbar_wait(bars + q, (unsigned)(k / NS) & 1u)) {
+            s_to[k & 1] = 1;
+            atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+            have = false;
+            continue;
+        }
+        const vec8 *sp = slots + ((long long)q * G + g) * slot;
+        if (p < p1) {
+            accum_block_smem<AR, S>(t, sp + a, sp + mm, m);
+            ++p;
+        } else {
+            accum_block_smem<AR, S>(z, sp + a, sp + mm, m);
+            store_row<AR, S>(P, i, a, t, z);
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+                t[l] = AR::zero();
+                z[l] = AR::zero();
+            }
+            i = MV_ROW(g, ++tsw);
+            have = i < T;
+            if (have) {
+                p = P.rp[i];
+                p1 = P.rp[i + 1];
+            }
+        }
+    }
+    // stages issued but not consumed (the plain arrivals past the last
+    // block, or, after a timeout in stage k-1, that stage and the ones after
+    // it): wait, bounded, so that no copy into this CTA's shared memory is in
+    // flight when it exits.  Stage k-1 is the latest stage of its slot, so
+    // its parity identifies its phase.
+    if (producer)
+        for (int j = k > 0 ? k - 1 : 0; j < issued; ++j) mbar_wait(bars + j % NS, (unsigned)(j / NS) & 1u);
+#undef MV_ROW
 }
 
 template <class AR>
@@ -149,34 +362,158 @@ int grid_for(long long work, int threads) {
     return (int)g;
 }
 
-template <class AR, int S>
-void run_matvec(const MatvecParams &P, cudaStream_t st) {
-    int groups = 256 / P.m;
-    int threads = groups * P.m;
-    threads = (threads + 31) / 32 * 32;
-    long long g = (P.T + groups - 1) / groups;
-    // chunk width: 8 columns for up to 3 stages, 4 beyond (register budget)
-    if (S <= 3)
-        k_matvec<AR, S, 8><<<(int)g, threads, 0, st>>>(P);
-    else
-        k_matvec<AR, S, 4><<<(int)g, threads, 0, st>>>(P);
+// Variants of the launch.  0-3: k_matvec with chunk width CH (columns whose
+// loads are in flight per thread) x threads per CTA.  4-6: k_matvec_pipe
+// with NS stages and the shared memory of one or two CTAs per SM.  Picked per
+// (m, s, arithmetic) by the autotuner below; all give identical results.
+struct MvVariant {
+    int ch, threads;  // k_matvec
+    int ns, per_sm;   // k_matvec_pipe (ns > 0)
+};
+const MvVariant kMvVariants[] = {{8, 256, 0, 0}, {4, 256, 0, 0}, {2, 256, 0, 0}, {4, 128, 0, 0},
+                                 {0, 0, 2, 1},   {0, 0, 3, 1},   {0, 0, 2, 2}};
+const int kNumMvVariants = 7;
+
+struct DevLimits {
+    int sms = 0, optin = 0, per_sm = 0;
+};
+DevLimits dev_limits() {
+    static std::mutex mu;
+    static DevLimits cached[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> g(mu);
+    DevLimits &L = cached[dev & 63];
+    if (L.sms == 0) {
+        cudaDeviceGetAttribute(&L.sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&L.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaDeviceGetAttribute(&L.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    }
+    return L;
 }
 
-template <class AR>
-void dispatch_s(int s, const MatvecParams &P, cudaStream_t st) {
-    switch (s) {
-        case 1: run_matvec<AR, 1>(P, st); break;
-        case 2: run_matvec<AR, 2>(P, st); break;
-        case 3: run_matvec<AR, 3>(P, st); break;
-        case 4: run_matvec<AR, 4>(P, st); break;
-        case 5: run_matvec<AR, 5>(P, st); break;
-        case 6: run_matvec<AR, 6>(P, st); break;
-        case 7: run_matvec<AR, 7>(P, st); break;
-        default: run_matvec<AR, 8>(P, st); break;
+// Groups per CTA of a pipelined variant (0: not applicable).  Needs m even
+// (16-byte multiples for the bulk copies) and 16-byte aligned operands.
+int pipe_groups(const MatvecParams &P, int s, const MvVariant &v) {
+    if (v.ns <= 0 || (P.m & 1)) return 0;
+    const uintptr_t al = (uintptr_t)P.J | (uintptr_t)P.M | (uintptr_t)P.x;
+    if (al & 15) return 0;
+    const DevLimits L = dev_limits();
+    const long long budget = v.per_sm == 1 ? L.optin : std::min<long long>(L.optin, L.per_sm / 2 - 1024);
+    const long long slot = ((long long)P.m * P.m + (long long)s * P.m) * sizeof(vec8);
+    long long G = (budget - IRK_MV_HEADER) / (v.ns * slot);
+    G = std::min<long long>(G, std::min(16, 256 / P.m));
+    return G < 1 ? 0 : (int)G;
+}
+
+template <class AR, int S, int CH>
+void run_matvec_ch(const MatvecParams &P, int max_threads, cudaStream_t st) {
+    int groups = std::max(1, max_threads / P.m);
+    int threads = (groups * P.m + 31) / 32 * 32;
+    long long g = (P.T + groups - 1) / groups;
+    k_matvec<AR, S, CH><<<(int)g, threads, 0, st>>>(P);
+}
+
+template <class AR, int S>
+void run_matvec_pipe(const MatvecParams &P, int G, int ns, int *err, cudaStream_t st) {
+    const size_t smem = mv_pipe_smem(P.m, S, G, ns);
+    irk_allow_max_smem((const void *)k_matvec_pipe<AR, S>);
+    const int threads = (G * P.m + 31) / 32 * 32;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_matvec_pipe<AR, S>, threads, smem);
+    const long long need = (P.T + G - 1) / G;
+    const long long grid = std::max(1LL, std::min<long long>(need, (long long)dev_limits().sms * std::max(1, per_sm)));
+    k_matvec_pipe<AR, S><<<(int)grid, threads, smem, st>>>(P, G, ns, err);
+}
+
+template <class AR, int S>
+void run_matvec(const MatvecParams &P, int variant, int *err, cudaStream_t st) {
+    const MvVariant v = kMvVariants[variant];
+    if (v.ns > 0) {
+        const int G = pipe_groups(P, S, v);
+        if (G > 0) {
+            run_matvec_pipe<AR, S>(P, G, v.ns, err, st);
+            return;
+        }
+        run_matvec_ch<AR, S, 8>(P, 256, st);  // not applicable here: the default variant
+    } else if (v.ch == 8) {
+        run_matvec_ch<AR, S, 8>(P, v.threads, st);
+    } else if (v.ch == 4) {
+        run_matvec_ch<AR, S, 4>(P, v.threads, st);
+    } else {
+        run_matvec_ch<AR, S, 2>(P, v.threads, st);
     }
 }
 
+template <class AR>
+void dispatch_s(int s, const MatvecParams &P, int variant, int *err, cudaStream_t st) {
+    switch (s) {
+        case 1: run_matvec<AR, 1>(P, variant, err, st); break;
+        case 2: run_matvec<AR, 2>(P, variant, err, st); break;
+        case 3: run_matvec<AR, 3>(P, variant, err, st); break;
+        case 4: run_matvec<AR, 4>(P, variant, err, st); break;
+        case 5: run_matvec<AR, 5>(P, variant, err, st); break;
+        case 6: run_matvec<AR, 6>(P, variant, err, st); break;
+        case 7: run_matvec<AR, 7>(P, variant, err, st); break;
+        default: run_matvec<AR, 8>(P, variant, err, st); break;
+    }
+}
+
+// Autotuner: the first operator product of a context whose (m, s,
+// arithmetic) has not been seen times every variant three times on the
+// context's own data (CUDA events on its stream) and keeps the fastest;
+// later contexts of the same class reuse the choice (process-wide cache).
+std::mutex g_tune_mu;
+std::map<long long, int> g_tune;
+
+int tune_key_variant(irk_ctx *c, const MatvecParams &P) {
+    // IRK_MATVEC_VARIANT=<0..6> pins the variant (tests compare them)
+    if (const char *pin = getenv("IRK_MATVEC_VARIANT")) {
+        const int v = atoi(pin);
+        if (v >= 0 && v < kNumMvVariants) return v;
+    }
+    const long long key = ((long long)c->m << 20) | ((long long)c->s << 4) | c->df;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) return it->second;
+    }
+    if (c->T < 64) return 0;  // too small to time meaningfully
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = 0;
+    float best_ms = 1e30f;
+    for (int v = 0; v < kNumMvVariants; ++v) {
+        float tot = 0.f;
+        for (int rep = 0; rep < 3; ++rep) {
+            cudaEventRecord(e0, c->stream);
+            if (c->df)
+                dispatch_s<ArDF>(c->s, P, v, c->d_err, c->stream);
+            else
+                dispatch_s<ArF64>(c->s, P, v, c->d_err, c->stream);
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) tot += ms;
+        }
+        if (tot < best_ms) {
+            best_ms = tot;
+            best = v;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tune[key] = best;
+    return best;
+}
+
 }  // namespace
+
+// chosen variant of a context's class (-1 before the first product)
+int matvec_variant(const irk_ctx *c) { return c->mv_variant; }
 
 int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt, int mode) {
     MatvecParams P;
@@ -194,10 +531,11 @@ int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt
     const double *C = (P.form == IRK_TRANSFORMED) ? c->Ainv : c->A;
     for (int q = 0; q < c->s * c->s; ++q) P.C[q] = make_kcoef(C[q]);
     P.mdt = make_kcoef(-dt);
+    if (c->mv_variant < 0) c->mv_variant = tune_key_variant(c, P);
     if (c->df)
-        dispatch_s<ArDF>(c->s, P, c->stream);
+        dispatch_s<ArDF>(c->s, P, c->mv_variant, c->d_err, c->stream);
     else
-        dispatch_s<ArF64>(c->s, P, c->stream);
+        dispatch_s<ArF64>(c->s, P, c->mv_variant, c->d_err, c->stream);
     c->launches++;
     return cuda_status(cudaGetLastError());
 }

@@ -49,7 +49,8 @@ class Stats(ctypes.Structure):
                 ("factor_ms", ctypes.c_double), ("solve_ms", ctypes.c_double),
                 ("kernel_launches", ctypes.c_longlong), ("matvec_ms", ctypes.c_double),
                 ("precond_ms", ctypes.c_double), ("ortho_ms", ctypes.c_double),
-                ("n_matvec", ctypes.c_int), ("n_precond", ctypes.c_int), ("n_ortho", ctypes.c_int)]
+                ("n_matvec", ctypes.c_int), ("n_precond", ctypes.c_int), ("n_ortho", ctypes.c_int),
+                ("matvec_variant", ctypes.c_int)]
 
 
 EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor", "irk_solve",
