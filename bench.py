@@ -219,6 +219,62 @@ def run_reference(args):
     return 0
 
 
+def dirk_comparison(P, dev, rp, ci, J, M, dt=0.1, reps=3):
+    """Equal-order IRK vs DIRK steps of M u' = J u on the benchmark mesh
+    (Sec. 5's comparison): RADAU23 vs DIRK33 and RADAU35 vs ESDIRK65.  One
+    step = the factorisation(s) and all stage solves; equivalent
+    multiplications = iterations x s (coupled system) or the sum of the
+    stages' iterations (DIRK)."""
+    import torch
+    from paper_1701_07181_gb300 import tableaux
+    T, m = P.T, P.m
+    u0 = torch.as_tensor(np.random.default_rng(17).standard_normal(T * m), device=dev)
+    # J u0 by block gather (input preparation, untimed)
+    rows = torch.repeat_interleave(torch.arange(T, device=dev), torch.diff(rp.long()))
+    Ju0 = torch.zeros(T, m, dtype=torch.float64, device=dev)
+    Ju0.index_add_(0, rows, torch.bmm(J.view(-1, m, m), u0.view(T, m)[ci.long()].unsqueeze(-1)).squeeze(-1))
+    Ju0 = Ju0.reshape(-1)
+    out = {}
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, s in (("RADAU23", 2), ("RADAU35", 3)):
+        S = irk.Solver(s, T, m, rp, ci, J, M, precond="uncoupled", factor_prec="fp32", krylov="df64",
+                       ordering="multicolor")
+        R = (dt * Ju0).repeat(s)
+        times, its = [], 0
+        for rep in range(reps + 1):
+            S.factor(2.0 * dt)  # invalidate the cached factor: every step refactors
+            torch.cuda.synchronize()
+            ev0.record()
+            W, its, rr, rc = S.solve(R, dt, rtol=RTOL)
+            ev1.record()
+            torch.cuda.synchronize()
+            if rep:
+                times.append(ev0.elapsed_time(ev1))
+        S.close()
+        out[name] = {"stages": s, "iters": its, "equivalent_multiplications": its * s,
+                     "ms_per_step": float(np.median(times))}
+    for name, fn in (("DIRK33", tableaux.dirk33), ("ESDIRK65", tableaux.esdirk65)):
+        A, b, _ = fn()
+        D = irk.Dirk(A, b, T, m, rp, ci, J, M, factor_prec="fp32", krylov="df64", ordering="multicolor")
+        times, its = [], []
+        for rep in range(reps + 1):
+            D.step(u0, 2.0 * dt, rtol=RTOL)  # so that the timed step refactors
+            torch.cuda.synchronize()
+            ev0.record()
+            u1, _, its, rr, rc = D.step(u0, dt, rtol=RTOL)
+            ev1.record()
+            torch.cuda.synchronize()
+            if rep:
+                times.append(ev0.elapsed_time(ev1))
+        D.close()
+        out[name] = {"stages": len(b), "implicit_stages": int(np.count_nonzero(np.diag(A))), "iters": its,
+                     "equivalent_multiplications": int(sum(its)), "ms_per_step": float(np.median(times))}
+    out["dt"] = dt
+    out["note"] = ("one step of M u' = J u on the benchmark mesh and blocks, each scheme refactored per step; "
+                   "FP32 factors, double-float Krylov, two-colour order, rtol 1e-8 per solve")
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -228,6 +284,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-dirk", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=60)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -398,6 +455,8 @@ def main():
             "roofline": roofline, "kernels": kernels, "e2e": e2e,
             "gpu_launches": acc["launches"], "clocks": clk,
             "last_solve": {"iters": st_last["iters"], "relres": st_last["relres"]}}
+    if not args.no_dirk and world == 1:
+        line["dirk_comparison"] = dirk_comparison(P, dev, rp, ci, J, M)
     if not args.no_serving and world == 1:
         from paper_1701_07181_gb300 import serve
         stream = inputs.serving_stream(args.serving_requests, rate=200.0, seed=11, elements=(1000, 10000),

@@ -276,6 +276,53 @@ IRK_API long long irk_group_device_bytes(const irk_group *g);
 
 IRK_API void irk_group_destroy(irk_group *g);
 
+/* ---------------------------------------------------------------------------
+ * Diagonally implicit Runge-Kutta steps (Sec. 3, Table 1, App. A: the DIRK
+ * comparison schemes DIRK33 and ESDIRK65, or any lower-triangular tableau).
+ *
+ * One step of M u' = J u (the linear(ised) system whose stage equations are
+ * M k_k = J (u0 + dt sum_j a_kj k_j)) with a lower-triangular A: stage k
+ * solves the single n x n system
+ *     (M - dt a_kk J) k_k = J (u0 + dt sum_{j<k} a_kj k_j),   n = T m,
+ * by restarted FGMRES preconditioned with the block ILU(0) of that matrix
+ * (the baseline DIRK solver of Sec. 5), or, when a_kk = 0 (the explicit
+ * first stage of an ESDIRK scheme), M k_k = J u0 (block-diagonal M: one
+ * iteration with its exact block factorisation); then
+ *     u1 = u0 + dt sum_k b_k k_k.
+ * Stages with the same a_kk share one factorisation per dt (one for all
+ * implicit stages of DIRK33 or ESDIRK65).  Sec. 5 counts the cost of a step
+ * as equivalent multiplications: the sum of the stages' iterations.
+ * -------------------------------------------------------------------------*/
+typedef struct irk_dirk irk_dirk;
+
+/* Create a DIRK stepper.
+ *   s         stages, 1 <= s <= 8; A host s*s row-major, lower triangular
+ *             (entries above the diagonal exactly 0), a_kk >= 0; b host s
+ *             weights.
+ *   T, m, row_ptr, col_idx, J, M, mem_space   as for irk_setup.
+ *   opt       NULL = defaults; restart, max_iter, factor_prec, krylov_arith,
+ *             stream, sweep, ordering and partitions are used; the
+ *             preconditioner is the block ILU(0) of each stage matrix
+ *             (IRK_PC_NONE in opt->precond switches it off).
+ * Copies everything (one single-stage context per distinct nonzero a_kk,
+ * plus one for explicit stages).  IRK_ERR_INVALID for a bad tableau. */
+IRK_API int irk_dirk_setup(irk_dirk **out, int s, const double *A, const double *b, int T, int m,
+                           const int32_t *row_ptr, const int32_t *col_idx, const double *J, const double *M,
+                           int mem_space, const irk_options *opt);
+
+/* One step from u0 (T*m values in mem_space) with step dt; every stage solve
+ * to relative residual rtol.
+ *   u1        T*m result in mem_space.
+ *   K         s*T*m stage derivatives k_1..k_s (stage-major) or NULL.
+ *   iters     s per-stage iteration counts (0 for explicit stages) or NULL.
+ *   relres    largest final relative residual over the stages or NULL.
+ * Returns IRK_OK, IRK_NOT_CONVERGED (a stage hit max_iter; u1 still formed
+ * from the last iterates) or an error. */
+IRK_API int irk_dirk_step(irk_dirk *d, const double *u0, double dt, double rtol, double *u1, double *K,
+                          int mem_space, int *iters, double *relres);
+
+IRK_API void irk_dirk_destroy(irk_dirk *d);
+
 /* Counters of the last irk_factor / irk_solve (host values). */
 typedef struct {
     int iters, cycles, levels_lower, levels_upper;

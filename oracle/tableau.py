@@ -11,6 +11,9 @@ benchmark's CPU-baseline leg; the library's CUDA path never imports it.
 * ``radau23()`` / ``radau35()`` are the closed forms printed in App. A.
 * ``shift_column_rule(Ainv)`` is the shift of Sec. 4.3.2,
   alpha_i = sum_{j != i} |(A^{-1})_{ji}|.
+* ``dirk33()`` / ``esdirk65()`` are the comparison DIRK schemes of Sec. 3
+  (Table 1) with the coefficients of App. A: DIRK33 from its closed form in
+  alpha, ESDIRK65 from the 16-digit values printed there.
 
 All arithmetic is FP64 numpy; root finding, polynomial integration and the
 matrix inverse are library primitives.
@@ -94,3 +97,36 @@ def stability_function(A, b, z):
     s = A.shape[0]
     one = np.ones(s, dtype=np.complex128)
     return 1.0 + z * (np.asarray(b) @ np.linalg.solve(np.eye(s) - z * A, one))
+
+
+def dirk33():
+    """DIRK33, App. A: three-stage, third-order, L-stable singly diagonally
+    implicit scheme (Sec. 3, Table 1), from the closed form of its diagonal
+    alpha (tau_2 = (1 + alpha)/2, b_1, b_2 quadratic in alpha)."""
+    th = math.atan(math.sqrt(2.0) / 4.0) / 3.0
+    al = 1.0 + math.sqrt(6.0) / 2.0 * math.sin(th) - math.sqrt(2.0) / 2.0 * math.cos(th)
+    tau2 = (1.0 + al) / 2.0
+    b1 = -(6.0 * al * al - 16.0 * al + 1.0) / 4.0
+    b2 = (6.0 * al * al - 20.0 * al + 5.0) / 4.0
+    A = np.array([[al, 0.0, 0.0], [tau2 - al, al, 0.0], [b1, b2, al]])
+    b = np.array([b1, b2, al])
+    c = np.array([al, tau2, 1.0])
+    return A, b, c
+
+
+def esdirk65():
+    """ESDIRK65, App. A: six stages (explicit first stage, the other five with
+    the same diagonal), fifth order, stiffly accurate (b = last row of A)."""
+    g = 0.2780538411364465
+    A = np.array([
+        [0.0, 0.0, 0.0, 0.0, 0.0, 0.0],
+        [0.2780538411364465, g, 0.0, 0.0, 0.0, 0.0],
+        [0.3137405401502951, 0.4363327154020044, g, 0.0, 0.0, 0.0],
+        [0.2741986534107860, -0.0164268277321164, 0.0048197082596452, g, 0.0, 0.0],
+        [-0.2441776975175844, -3.3203529439447852, 0.0477747285706825, 3.2974431145814931, g, 0.0],
+        [-0.2786732780227907, 1.8929947094010862, -0.1280948204262490, -1.3574693381380240,
+         0.5931888860495311, g],
+    ])
+    b = A[-1].copy()
+    c = np.array([0.0, 0.556107682272893, 1.028127096688746, 0.540645375074761, 0.058741042826253, 1.0])
+    return A, b, c

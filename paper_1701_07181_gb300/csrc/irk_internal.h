@@ -104,6 +104,11 @@ struct irk_ctx {
 // ---- launchers (k_matvec.cu) ----
 // y = B x (mode 0) or y = rhs - B x (mode 1); form: IRK_TRANSFORMED / UNTRANSFORMED
 int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt, int mode);
+// y = (I (x) J) x in the context's arithmetic (internal layout)
+int launch_jacobian(irk_ctx *c, const vec8 *x, vec8 *y);
+// operator-product form value for the Jacobian alone (internal; beside the
+// public IRK_TRANSFORMED / IRK_UNTRANSFORMED)
+#define IRK_FORM_JACOBIAN 2
 // raise a kernel's dynamic shared-memory limit to the device maximum (once)
 int irk_allow_max_smem(const void *func);
 // stage-major binary64 <-> element-interleaved vec8

@@ -98,17 +98,24 @@ struct AsmTables {
 };
 
 template <class C>
-__global__ void k_assemble(long long nnz, int m, const AsmEntry *ent, const vec8 *J, const vec8 *M, int df,
-                           AsmTables tab, C *vals) {
-    const long long mm = (long long)m * m;
-    const long long total = nnz * mm;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        long long q = e / mm, r = e - q * mm;
-        AsmEntry a = ent[q];
-        C v = C(0);
-        if (a.mi >= 0) v += (C)tab.cm[a.cm_id] * CT<C>::from_store(M[(long long)a.mi * mm + r], df);
-        if (a.jp >= 0) v += (C)tab.cj[a.cj_id] * CT<C>::from_store(J[(long long)a.jp * mm + r], df);
-        vals[e] = v;
+__global__ void __launch_bounds__(256) k_assemble(long long nnz, int m, const AsmEntry *ent, const vec8 *J,
+                                                  const vec8 *M, int df, AsmTables tab, C *vals) {
+    // one block per CTA iteration: the entry and its coefficients are
+    // uniform, the threads stream the block's m*m values
+    const int mm = m * m;
+    for (long long q = blockIdx.x; q < nnz; q += gridDim.x) {
+        const AsmEntry a = ent[q];
+        const vec8 *Mb = a.mi >= 0 ? M + (long long)a.mi * mm : nullptr;
+        const vec8 *Jb = a.jp >= 0 ? J + (long long)a.jp * mm : nullptr;
+        const C cm = Mb ? (C)tab.cm[a.cm_id] : C(0);
+        const C cj = Jb ? (C)tab.cj[a.cj_id] : C(0);
+        C *out = vals + q * mm;
+        for (int r = threadIdx.x; r < mm; r += blockDim.x) {
+            C v = C(0);
+            if (Mb) v += cm * CT<C>::from_store(Mb[r], df);
+            if (Jb) v += cj * CT<C>::from_store(Jb[r], df);
+            out[r] = v;
+        }
     }
 }
 
@@ -1264,7 +1271,7 @@ static int factor_impl(irk_ctx *c, double dt) {
             tab.cm[0] = 1.0;
             for (int q = 0; q < s * s; ++q) tab.cj[q] = -dt * c->A[q];
         }
-        k_assemble<C><<<grid_cap(P.nnz * c->m * c->m), 256, 0, c->stream>>>(P.nnz, c->m, P.d_asm, c->d_J, c->d_M,
+        k_assemble<C><<<grid_cap(P.nnz * 256), 256, 0, c->stream>>>(P.nnz, c->m, P.d_asm, c->d_J, c->d_M,
                                                                            c->df, tab, (C *)P.d_vals);
     }
     c->launches++;

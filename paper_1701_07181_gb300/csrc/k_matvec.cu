@@ -17,6 +17,7 @@
 // values) are read by all m threads of the group at the same address
 // (a broadcast through L1).
 #include <stdlib.h>
+#include <string.h>
 
 #include <algorithm>
 #include <map>
@@ -59,7 +60,7 @@ __device__ __forceinline__ void accum_block(typename AR::acc (&dst)[S], const ve
 
 // Mixes the per-stage sums of row i (t_l = sum_j J_ij x_{l,j},
 // z_l = M_i x_{l,i}) into the s outputs of thread row a and stores them
-// (mode 1: rhs - y).
+// (mode 1: rhs - y).  IRK_FORM_JACOBIAN: y_k = t_k (the Jacobian alone).
 template <class AR, int S>
 __device__ __forceinline__ void store_row(const MatvecParams &P, long long i, int a, const typename AR::acc (&t)[S],
                                           const typename AR::acc (&z)[S]) {
@@ -77,7 +78,9 @@ __device__ __forceinline__ void store_row(const MatvecParams &P, long long i, in
 #pragma unroll
     for (int k = 0; k < S; ++k) {
         acc o = AR::zero();
-        if (P.form == IRK_TRANSFORMED) {
+        if (P.form == IRK_FORM_JACOBIAN) {
+            AR::add_to(o, tv[k]);
+        } else if (P.form == IRK_TRANSFORMED) {
 #pragma unroll
             for (int l = 0; l < S; ++l) {
                 const KCoef &cc = P.C[k * S + l];
@@ -122,7 +125,7 @@ __global__ void __launch_bounds__(256) k_matvec(MatvecParams P) {
         const int p0 = P.rp[i], p1 = P.rp[i + 1];
         for (int p = p0; p < p1; ++p)
             accum_block<AR, S, CH>(t, P.J + (long long)p * mm + a, P.x + (long long)P.ci[p] * sm, m);
-        accum_block<AR, S, CH>(z, P.M + i * mm + a, P.x + i * sm, m);
+        if (P.form != IRK_FORM_JACOBIAN) accum_block<AR, S, CH>(z, P.M + i * mm + a, P.x + i * sm, m);
         store_row<AR, S>(P, i, a, t, z);
     }
 }
@@ -536,6 +539,31 @@ int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt
         dispatch_s<ArDF>(c->s, P, c->mv_variant, c->d_err, c->stream);
     else
         dispatch_s<ArF64>(c->s, P, c->mv_variant, c->d_err, c->stream);
+    c->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+// y = (I_s (x) J) x: the Jacobian product alone (right-hand sides of DIRK
+// stages), register-streaming launch, the mass blocks not read.
+int launch_jacobian(irk_ctx *c, const vec8 *x, vec8 *y) {
+    MatvecParams P;
+    memset(&P, 0, sizeof(P));
+    P.T = c->T;
+    P.m = c->m;
+    P.form = IRK_FORM_JACOBIAN;
+    P.mode = 0;
+    P.rp = c->d_rp;
+    P.ci = c->d_ci;
+    P.J = c->d_J;
+    P.M = c->d_M;
+    P.x = x;
+    P.rhs = nullptr;
+    P.y = y;
+    P.mdt = make_kcoef(0.0);
+    if (c->df)
+        dispatch_s<ArDF>(c->s, P, 0, c->d_err, c->stream);
+    else
+        dispatch_s<ArF64>(c->s, P, 0, c->d_err, c->stream);
     c->launches++;
     return cuda_status(cudaGetLastError());
 }

@@ -57,7 +57,7 @@ EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor"
            "irk_apply_operator", "irk_apply_precond", "irk_get_stats", "irk_destroy",
            "irk_strerror", "irk_apply_precond_noalloc", "irk_group_create", "irk_group_submit",
            "irk_group_step", "irk_group_query", "irk_group_collect", "irk_group_device_bytes",
-           "irk_group_destroy"]
+           "irk_group_destroy", "irk_dirk_setup", "irk_dirk_step", "irk_dirk_destroy"]
 
 
 def load():
@@ -94,6 +94,10 @@ def load():
         lib.irk_group_device_bytes.restype = ctypes.c_longlong
         lib.irk_group_destroy.argtypes = [P]
         lib.irk_group_destroy.restype = None
+        lib.irk_dirk_setup.argtypes = [ctypes.POINTER(P), I, P, P, I, I, P, P, P, P, I, ctypes.POINTER(Options)]
+        lib.irk_dirk_step.argtypes = [P, P, D, D, P, P, I, P, ctypes.POINTER(D)]
+        lib.irk_dirk_destroy.argtypes = [P]
+        lib.irk_dirk_destroy.restype = None
         _lib = lib
         return lib
 
@@ -332,6 +336,84 @@ class Group:
     def close(self):
         if getattr(self, "_h", None):
             self._lib.irk_group_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+class Dirk:
+    """Diagonally implicit Runge-Kutta stepper of M u' = J u
+    (irk_dirk_setup ... irk_dirk_destroy): stage k solves
+    (M - dt a_kk J) k_k = J (u0 + dt sum_{j<k} a_kj k_j) with FGMRES and the
+    block ILU(0) of the stage matrix; u1 = u0 + dt sum_k b_k k_k."""
+
+    def __init__(self, A, b, T, m, row_ptr, col_idx, J, M, factor_prec="fp64", krylov="fp64", restart=30,
+                 max_iter=3000, stream=None, sweep="auto", ordering="natural", precond="coupled"):
+        lib = load()
+        self._lib = lib
+        self._A = np.ascontiguousarray(A, dtype=np.float64)
+        self._b = np.ascontiguousarray(b, dtype=np.float64)
+        self.s = int(self._b.size)
+        self.T, self.m = int(T), int(m)
+        self.n = self.T * self.m
+        opt = Options()
+        lib.irk_default_options(ctypes.byref(opt))
+        opt.restart = int(restart)
+        opt.max_iter = int(max_iter)
+        opt.precond = PRECOND[precond] if isinstance(precond, str) else int(precond)
+        opt.factor_prec = FACTOR_PREC[factor_prec] if isinstance(factor_prec, str) else int(factor_prec)
+        opt.krylov_arith = KRYLOV[krylov] if isinstance(krylov, str) else int(krylov)
+        if stream is not None:
+            opt.stream = ctypes.c_void_p(int(stream))
+        opt.sweep = {"auto": 0, "levels": 1}[sweep]
+        opt.ordering = {"natural": 0, "multicolor": 1}[ordering]
+        rp, k1, sp1 = _ptr(row_ptr, np.int32)
+        ci, k2, sp2 = _ptr(col_idx, np.int32)
+        Jp, k3, sp3 = _ptr(J, np.float64)
+        Mp, k4, sp4 = _ptr(M, np.float64)
+        if len({sp1, sp2, sp3, sp4}) != 1:
+            raise ValueError("pattern and values must all be host arrays or all CUDA tensors")
+        h = ctypes.c_void_p()
+        rc = lib.irk_dirk_setup(ctypes.byref(h), self.s, self._A.ctypes.data_as(ctypes.c_void_p),
+                                self._b.ctypes.data_as(ctypes.c_void_p), self.T, self.m, rp, ci, Jp, Mp, sp1,
+                                ctypes.byref(opt))
+        if rc != IRK_OK:
+            raise IrkError(rc, "irk_dirk_setup")
+        self._h = h
+
+    def step(self, u0, dt, rtol=1e-8, want_K=False):
+        """(u1, K or None, per-stage iterations, worst relres, status)."""
+        up, keep, sp = _ptr(u0, np.float64)
+        if sp == IRK_DEVICE:
+            import torch
+            u1 = torch.empty(self.n, dtype=torch.float64, device=u0.device)
+            K = torch.empty(self.s * self.n, dtype=torch.float64, device=u0.device) if want_K else None
+        else:
+            u1 = np.empty(self.n)
+            K = np.empty(self.s * self.n) if want_K else None
+        u1p, k1, _ = _ptr(u1, np.float64)
+        Kp = _ptr(K, np.float64)[0] if K is not None else None
+        its = np.zeros(self.s, dtype=np.int32)
+        rr = ctypes.c_double(0.0)
+        rc = self._lib.irk_dirk_step(self._h, up, float(dt), float(rtol), u1p, Kp, sp,
+                                     its.ctypes.data_as(ctypes.c_void_p), ctypes.byref(rr))
+        if rc not in (IRK_OK, IRK_NOT_CONVERGED):
+            raise IrkError(rc, "irk_dirk_step")
+        return u1, K, [int(x) for x in its], rr.value, rc
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.irk_dirk_destroy(self._h)
             self._h = None
 
     def __del__(self):
