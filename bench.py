@@ -66,9 +66,11 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_record(kernel):
-    """Per-launch DRAM bytes of a kernel from the committed ncu summary, or
-    None when absent or taken on a different source of the kernel."""
+def traffic_record(phase):
+    """DRAM bytes of one unit of a phase (matvec: one launch; precond_sweeps:
+    one application; factorization: one factorisation) from the committed ncu
+    summary, or None when absent or taken on a different source of the
+    kernels."""
     path = os.path.join(ROOT, "profiles", "dram_traffic_c1.txt")
     if not os.path.exists(path):
         return None
@@ -285,6 +287,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-dirk", action="store_true")
+    ap.add_argument("--uneven-requests", type=int, default=128)
     ap.add_argument("--serving-requests", type=int, default=60)
     args = ap.parse_args()
     if args.impl == "reference":
@@ -434,12 +437,12 @@ def main():
         roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                     "frac": achieved / alu_peak if achieved else None,
                     "peak_source": "FP32 CUDA-core peak from unit counts and max clock (152 x 128 x 2 x 2.07 GHz)",
-                    "traffic": traffic_record("k_factor_level2")}
+                    "traffic": traffic_record("factorization")}
     else:
         achieved = dk["achieved_gbs"]
         roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
                     "frac": achieved / peak if achieved else None, "peak_source": peak_kind + " hbm_gbs",
-                    "traffic": traffic_record("k_sweep" if dominant == "precond_sweeps" else "k_matvec")}
+                    "traffic": traffic_record(dominant)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "df64 Krylov / f32 factors",
@@ -457,6 +460,25 @@ def main():
             "last_solve": {"iters": st_last["iters"], "relres": st_last["relres"]}}
     if not args.no_dirk and world == 1:
         line["dirk_comparison"] = dirk_comparison(P, dev, rp, ci, J, M)
+    if not args.no_serving and world == 1 and args.uneven_requests > 0:
+        # batched uneven: independent 2D meshes of 500-5000 triangles, p 1..3,
+        # s 2..3, all submitted at once (continuous batching of a backlog)
+        from paper_1701_07181_gb300 import serve
+        ub = inputs.batched_uneven(args.uneven_requests, seed=5)
+        for q in ub:
+            q["arrival"] = 0.0
+        probs = serve.prepare(ub, dev)
+        torch.cuda.synchronize()
+        recs_b, sb = serve.run_stream(ub, probs, budget_bytes=120 << 30)
+        recs_f, sf = serve.run_fifo(ub, probs)
+        line["batched_uneven"] = {
+            "requests": sb.n, "meshes": "2D periodic, 500-5000 triangles, p 1..3 (m 12/24/40), s 2..3, dt 0.1",
+            "batched": {"solves_per_s": sb.solves_per_s, "wall_s": sb.wall_s, "groups": sb.extra["groups"],
+                        "all_converged": all(r.status == 0 for r in recs_b)},
+            "fifo_plain_fp64": {"solves_per_s": sf.solves_per_s, "wall_s": sf.wall_s,
+                                "all_converged": all(r.status == 0 for r in recs_f)},
+        }
+        del probs
     if not args.no_serving and world == 1:
         from paper_1701_07181_gb300 import serve
         stream = inputs.serving_stream(args.serving_requests, rate=200.0, seed=11, elements=(1000, 10000),

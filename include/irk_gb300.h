@@ -137,6 +137,13 @@ typedef struct {
     const int32_t *partition; /* optional host array of T partition ids (overrides
                           partitions); blocks coupling two different ids are
                           dropped from the preconditioner; copied at irk_setup */
+    int stage_jacobians; /* 0 (default): one J shared by all stages, J holds
+                          nnzb*m*m values.  1: one Jacobian per stage (Sec. 4.1,
+                          J_k at the state of stage k), J holds s*nnzb*m*m
+                          values, stage after stage; stage k's rows use J_k
+                          (transformed: A^{-1} (x) M - dt diag(J_1..J_s);
+                          untransformed: I (x) M - dt [a_kl J_k]).  Not
+                          accepted by irk_group_create. */
 } irk_options;
 
 /* Fill *opt with the defaults listed above. */
@@ -156,7 +163,8 @@ IRK_API int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const
               const int32_t *col_idx, const double *J, const double *M, int mem_space,
               const irk_options *opt);
 
-/* Replace the values of J and M (same pattern), e.g. at a new Newton
+/* Replace the values of J and M (same pattern; J holds s Jacobians when
+ * the context was set up with stage_jacobians = 1), e.g. at a new Newton
  * iterate (Sec. 4.1).  Invalidates the factors. */
 IRK_API int irk_update_values(irk_ctx *ctx, const double *J, const double *M, int mem_space);
 

@@ -162,13 +162,13 @@ int sync_err(irk_ctx *c) {
 // enough, else through a temporary device buffer.
 int load_values(irk_ctx *c, const double *J, const double *M, int mem_space) {
     const long long mm = (long long)c->m * c->m;
-    const long long nJ = (long long)c->nnzb * mm, nM = (long long)c->T * mm;
+    const long long nJ = (long long)c->nJ * c->nnzb * mm, nM = (long long)c->T * mm;
     const long long need = nJ > nM ? nJ : nM;
     double *tmp = nullptr;
     int rc = cuda_status(cudaMalloc(&tmp, (size_t)need * sizeof(double)));
     if (rc) return rc;
     if ((rc = copy_in(tmp, J, (size_t)nJ * sizeof(double), mem_space, c->stream)) == IRK_OK &&
-        (rc = launch_convert_blocks(c, tmp, c->d_J, c->nnzb)) == IRK_OK &&
+        (rc = launch_convert_blocks(c, tmp, c->d_J, (long long)c->nJ * c->nnzb)) == IRK_OK &&
         (rc = copy_in(tmp, M, (size_t)nM * sizeof(double), mem_space, c->stream)) == IRK_OK &&
         (rc = launch_convert_blocks(c, tmp, c->d_M, c->T)) == IRK_OK)
         rc = cuda_status(cudaStreamSynchronize(c->stream));
@@ -264,6 +264,7 @@ void irk_default_options(irk_options *o) {
     o->ordering = IRK_ORDER_NATURAL;
     o->partitions = 0;
     o->partition = nullptr;
+    o->stage_jacobians = 0;
 }
 
 const char *irk_strerror(int code) {
@@ -301,7 +302,8 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
         c->opt.precond < IRK_PC_NONE || c->opt.precond > IRK_PC_ELEMENT || c->opt.factor_prec < 0 ||
         c->opt.factor_prec > IRK_FACTOR_BF16 || c->opt.krylov_arith < 0 || c->opt.krylov_arith > 1 ||
         c->opt.formulation < 0 || c->opt.formulation > 1 || c->opt.sweep < 0 || c->opt.sweep > 1 ||
-        c->opt.ordering < 0 || c->opt.ordering > 1 || c->opt.partitions < 0 ||
+        c->opt.ordering < 0 || c->opt.ordering > 1 || c->opt.partitions < 0 || c->opt.stage_jacobians < 0 ||
+        c->opt.stage_jacobians > 1 ||
         (c->opt.precond == IRK_PC_UNCOUPLED && c->opt.formulation != IRK_TRANSFORMED)) {
         delete c;
         return IRK_ERR_INVALID;
@@ -312,6 +314,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
     c->m = m;
     c->df = c->opt.krylov_arith == IRK_KRYLOV_DF64;
     c->fprec = c->opt.factor_prec;
+    c->nJ = (c->opt.stage_jacobians && s > 1) ? s : 1;
     cudaGetDevice(&c->dev);
     // pattern: host copy and validation
     c->h_rp.resize(T + 1);
@@ -384,7 +387,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
     c->red_blocks = 152 * 4;
     bool ok = cudaMalloc(&c->d_rp, sizeof(int) * (T + 1)) == cudaSuccess &&
               cudaMalloc(&c->d_ci, sizeof(int) * (c->nnzb > 0 ? c->nnzb : 1)) == cudaSuccess &&
-              cudaMalloc(&c->d_J, sizeof(vec8) * (size_t)c->nnzb * mm) == cudaSuccess &&
+              cudaMalloc(&c->d_J, sizeof(vec8) * (size_t)c->nJ * c->nnzb * mm) == cudaSuccess &&
               cudaMalloc(&c->d_M, sizeof(vec8) * (size_t)T * mm) == cudaSuccess &&
               cudaMalloc(&c->d_V, sizeof(vec8) * (size_t)c->N * (R + 1)) == cudaSuccess &&
               cudaMalloc(&c->d_Z, sizeof(vec8) * (size_t)c->N * R) == cudaSuccess &&

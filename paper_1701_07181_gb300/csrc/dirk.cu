@@ -92,6 +92,7 @@ int irk_dirk_setup(irk_dirk **out, int s, const double *A, const double *b, int 
     o.formulation = IRK_UNTRANSFORMED;
     o.precond = (opt && opt->precond == IRK_PC_NONE) ? IRK_PC_NONE : IRK_PC_COUPLED;
     o.shift = nullptr;
+    o.stage_jacobians = 0;
     d->stream = (cudaStream_t)o.stream;
     std::vector<double> gam;
     int rc = IRK_OK;

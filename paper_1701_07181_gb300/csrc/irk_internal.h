@@ -46,6 +46,11 @@ struct PcSystem {
     // level schedules (rows grouped by level; host copies of the level bounds)
     std::vector<int> lo_ptr, up_ptr;
     int *d_lo_rows = nullptr, *d_up_rows = nullptr;
+    // uncoupled kind with every stage's upper blocks equal to -dt J (no
+    // factor update reaches them): backward levels as stage-0 rows only
+    int shared_upper = 0;
+    std::vector<int> up0_ptr;
+    int *d_up0_rows = nullptr;
     // values, column-major blocks: working precision (double or float)
     void *d_vals = nullptr, *d_dinv = nullptr;
     // bf16 copies used by the sweeps when factor_prec == IRK_FACTOR_BF16
@@ -67,6 +72,7 @@ struct irk_ctx {
     int dev = 0;
     cudaStream_t stream = nullptr;
     int s = 0, T = 0, m = 0, nnzb = 0;
+    int nJ = 1;  // Jacobians stored: 1 (shared by the stages) or s (one per stage)
     long long n = 0, N = 0;  // n = T m, N = s n
     double A[IRK_MAX_S * IRK_MAX_S], Ainv[IRK_MAX_S * IRK_MAX_S], shift[IRK_MAX_S];
     irk_options opt;

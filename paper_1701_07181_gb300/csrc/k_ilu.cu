@@ -16,6 +16,8 @@
 // with partial pivoting), so the backward sweep is two block products.
 #include <cuda_bf16.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <cstring>
 #include <mutex>
@@ -51,6 +53,22 @@ int allow_max_smem(const void *func) {
         return IRK_ERR_CUDA;
     done.push_back(func);
     return IRK_OK;
+}
+
+// Threads per inversion CTA (k_factor_diag) and the level width from which a
+// level's inversions leave the product kernel; IRK_GJ_THREADS and
+// IRK_GJ_SPLIT_MIN override them (measurement).
+int env_int(const char *name, int dflt) {
+    const char *v = getenv(name);
+    return v ? atoi(v) : dflt;
+}
+int gj_threads() {
+    static const int t = std::max(32, std::min(256, env_int("IRK_GJ_THREADS", 128)));
+    return t;
+}
+int gj_split_min() {
+    static const int n = env_int("IRK_GJ_SPLIT_MIN", 2048);
+    return n;
 }
 
 // ---------------------------------------------------------------------------
@@ -125,7 +143,8 @@ __global__ void __launch_bounds__(256) k_assemble(long long nnz, int m, const As
 //   form 1: [k==l][diag] M_i[a][c] - dt C_kl J_p[a][c]
 template <class C>
 __global__ void k_assemble_elem(long long nnzb, int s, int m, int form, const int *rowof, const int *ci,
-                                const vec8 *J, const vec8 *M, int df, AsmTables tab, double dt, C *vals) {
+                                const vec8 *J, long long jstride, const vec8 *M, int df, AsmTables tab, double dt,
+                                C *vals) {
     const long long sm = (long long)s * m, blk = sm * sm, mm = (long long)m * m;
     const long long total = nnzb * blk;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
@@ -135,7 +154,8 @@ __global__ void k_assemble_elem(long long nnzb, int s, int m, int form, const in
         int k = (int)(rowbig / m), a = (int)(rowbig - (long long)k * m);
         int i = rowof[p];
         bool diag = (ci[p] == i);
-        double Jv = (double)CT<C>::from_store(J[p * mm + (long long)c * m + a], df);
+        // stage k's rows use J_k (jstride = 0: one J shared by the stages)
+        double Jv = (double)CT<C>::from_store(J[k * jstride + p * mm + (long long)c * m + a], df);
         double Mv = diag ? (double)CT<C>::from_store(M[(long long)i * mm + (long long)c * m + a], df) : 0.0;
         double coef = tab.cm[k * s + l];
         double v = (form == 0) ? coef * Mv - (k == l ? dt * Jv : 0.0) : (k == l ? Mv : 0.0) - dt * coef * Jv;
@@ -557,7 +577,7 @@ __device__ __forceinline__ void load_pair(C *d1, const C *s1, C *d2, const C *s2
 template <class C>
 __global__ void __launch_bounds__(256) k_factor_level2(const int *rows, int b, const int *rp, const int *ci,
                                                        const int *diag, const int *upd_ptr, const int *upd,
-                                                       C *vals, C *dinv, int *err) {
+                                                       C *vals, C *dinv, int *err, int do_inverse) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int bb = b * b;
     C *X = reinterpret_cast<C *>(smem_raw);  // b * (b + 1): also the padded copy for Gauss-Jordan
@@ -589,6 +609,33 @@ __global__ void __launch_bounds__(256) k_factor_level2(const int *rows, int b, c
         vals[(long long)dpos * bb + e] = D[e];
         X[col * (b + 1) + row] = D[e];
     }
+    if (!do_inverse) return;  // k_factor_diag inverts it
+    __syncthreads();
+    const bool ok = gauss_jordan3(X, Y, b, fcol, b + 1);
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) dinv[(long long)R * bb + e] = Y[e];
+    if (!ok && threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_SINGULAR);
+}
+
+// D_R^{-1} for a list of rows whose diagonal block is final (rows without
+// lower entries, or rows whose updates k_factor_level2 applied): the same
+// Gauss-Jordan (gauss_jordan3) by a small CTA.  The inversion is a chain of
+// b barrier-separated pivot steps, so its throughput grows with the number of
+// inversions an SM holds at once; the product kernel's 256-thread CTAs hold
+// six, 128-thread CTAs with only the two b x b work arrays twice as many.
+template <class C>
+__global__ void __launch_bounds__(256) k_factor_diag(const int *rows, int b, const int *diag, const C *vals, C *dinv,
+                                                     int *err) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int bb = b * b;
+    C *X = reinterpret_cast<C *>(smem_raw);  // b * (b + 1), padded columns
+    C *Y = X + bb + b;
+    C *fcol = Y + bb;
+    const int R = rows[blockIdx.x];
+    const C *D = vals + (long long)diag[R] * bb;
+    for (int e = threadIdx.x; e < bb; e += blockDim.x) {
+        const int col = e / b, row = e - col * b;
+        X[col * (b + 1) + row] = D[e];
+    }
     __syncthreads();
     const bool ok = gauss_jordan3(X, Y, b, fcol, b + 1);
     for (int e = threadIdx.x; e < bb; e += blockDim.x) dinv[(long long)R * bb + e] = Y[e];
@@ -600,6 +647,12 @@ __global__ void k_to_bf16(long long n, const C *src, __nv_bfloat16 *dst) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
         dst[e] = __float2bfloat16_rn((float)src[e]);
 }
+
+// Explicitly fused multiply-add: the sweeps' dot products round the same way
+// in every kernel that computes them (the compiler may otherwise fuse a*b+c
+// in one kernel and not in another).
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
 
 // sum_c B[c][a] x[c] for a column-major block (thread's row a pre-applied to
 // B): chunks of 8 columns with every load of a chunk issued before its FMAs
@@ -617,8 +670,8 @@ __device__ __forceinline__ C block_col_dot(const F *B, const C *x, int b) {
         }
 #pragma unroll
         for (int u = 0; u < 8; u += 2) {
-            s0 += bv[u] * xv[u];
-            s1 += bv[u + 1] * xv[u + 1];
+            s0 = fma_rn(bv[u], xv[u], s0);
+            s1 = fma_rn(bv[u + 1], xv[u + 1], s1);
         }
     }
     return s0 + s1;
@@ -675,6 +728,81 @@ __global__ void __launch_bounds__(256) k_sweep_bwd(const int *rows, int nrows, i
     C acc = block_col_dot<C>(dinv + (long long)R * bb + a, t + g * b, b);
     y[voff[R] + a] = acc;
     AR::st(z + voff[R] + a, CT<C>::template to_vec<AR>(acc));
+}
+
+// Backward sweep of the uncoupled preconditioner with the upper blocks read
+// once for all stages.  Its s stage systems share the pattern, and where no
+// factor update targets an upper block (no element with two mutually
+// adjacent neighbours, checked at set-up) every stage's upper block is the
+// same -dt J_ij; the item is an element row of stage 0, the block is loaded
+// once and applied to the s stage vectors.  Per stage the sums run in
+// block_col_dot's order (8-column chunks, two accumulators), so the result
+// equals k_sweep_bwd's bit for bit.
+template <class C, class F, int S>
+__device__ __forceinline__ void block_col_dot_multi(const F *B, const C *const (&x)[S], int b, C (&out)[S]) {
+    C s0[S], s1[S];
+#pragma unroll
+    for (int k = 0; k < S; ++k) s0[k] = s1[k] = C(0);
+    for (int c0 = 0; c0 < b; c0 += 8) {
+        C bv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) bv[u] = c0 + u < b ? (C)ldfac(B + (long long)(c0 + u) * b) : C(0);
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            C xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) xv[u] = c0 + u < b ? x[k][c0 + u] : C(0);
+#pragma unroll
+            for (int u = 0; u < 8; u += 2) {
+                s0[k] = fma_rn(bv[u], xv[u], s0[k]);
+                s1[k] = fma_rn(bv[u + 1], xv[u + 1], s1[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < S; ++k) out[k] = s0[k] + s1[k];
+}
+
+template <class AR, class C, class F, int S>
+__global__ void __launch_bounds__(256) k_sweep_bwd_shared(const int *rows0, int nrows, int b, int T,
+                                                          const int *rp, const int *ci, const int *voff,
+                                                          const F *vals, const F *dinv, C *y, vec8 *z) {
+    constexpr int s = S;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    C *t = reinterpret_cast<C *>(smem_raw);  // groups * s * b
+    const int groups = blockDim.x / b;
+    const int g = threadIdx.x / b, a = threadIdx.x - g * b;
+    const int idx = blockIdx.x * groups + g;
+    const bool active = (g < groups) && (idx < nrows);
+    const long long bb = (long long)b * b;
+    int R0 = 0;
+    if (active) {
+        R0 = rows0[idx];
+        C acc[S];
+#pragma unroll
+        for (int k = 0; k < S; ++k) acc[k] = y[voff[k * T + R0] + a];
+        for (int p = rp[R0 + 1] - 1; p >= rp[R0]; --p) {
+            const int col = ci[p];
+            if (col <= R0) break;
+            const C *x[S];
+#pragma unroll
+            for (int k = 0; k < S; ++k) x[k] = y + voff[k * T + col];
+            C d[S];
+            block_col_dot_multi<C, F, S>(vals + (long long)p * bb + a, x, b, d);
+#pragma unroll
+            for (int k = 0; k < S; ++k) acc[k] -= d[k];
+        }
+#pragma unroll
+        for (int k = 0; k < S; ++k) t[(g * s + k) * b + a] = acc[k];
+    }
+    __syncthreads();
+    if (!active) return;
+    for (int k = 0; k < s; ++k) {
+        const int R = k * T + R0;
+        const C v = block_col_dot<C>(dinv + (long long)R * bb + a, t + (g * s + k) * b, b);
+        y[voff[R] + a] = v;
+        AR::st(z + voff[R] + a, CT<C>::template to_vec<AR>(v));
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1135,14 +1263,16 @@ int pc_build_pattern(irk_ctx *c) {
                     for (int l = 0; l < k; ++l) mass(l);
                 int lfirst = (P.kind == IRK_PC_COUPLED && !transformed) ? 0 : k;
                 int llast = (P.kind == IRK_PC_COUPLED && !transformed) ? s - 1 : k;
+                // stage k's rows use J_k when the stages have their own Jacobians
+                const int jk = c->nJ > 1 ? k * c->nnzb : 0;
                 for (int l = lfirst; l <= llast; ++l)
                     for (const auto &nq : nb_new) {
                         const int p = nq.second, j = ci[p];
                         h.ci.push_back(l * T + nq.first);
-                        if (transformed)  // d_k M - dt J  (uncoupled: d_k = A^{-1}_kk + alpha_k)
-                            h.asmv.push_back(AsmEntry{p, j == e ? e : -1, k * s + k, 0});
-                        else  // [k==l][e==j] M - dt a_kl J
-                            h.asmv.push_back(AsmEntry{p, (j == e && l == k) ? e : -1, 0, k * s + l});
+                        if (transformed)  // d_k M - dt J_k  (uncoupled: d_k = A^{-1}_kk + alpha_k)
+                            h.asmv.push_back(AsmEntry{jk + p, j == e ? e : -1, k * s + k, 0});
+                        else  // [k==l][e==j] M - dt a_kl J_k
+                            h.asmv.push_back(AsmEntry{jk + p, (j == e && l == k) ? e : -1, 0, k * s + l});
                     }
                 if (P.kind == IRK_PC_COUPLED && transformed)
                     for (int l = k + 1; l < s; ++l) mass(l);
@@ -1185,16 +1315,38 @@ int pc_build_pattern(irk_ctx *c) {
     }
     levels_lower(h, h.lo_rows, h.lo_ptr);
     levels_upper(h, h.up_rows, h.up_ptr);
+    // uncoupled kind: do all stages keep -dt J_ij as upper blocks (no factor
+    // update targets an upper block)?  Then the backward sweep may read one
+    // copy for all stages, and its items are the stage-0 rows of each level.
+    std::vector<int> up0_rows, up0_ptr;
+    P.shared_upper = 0;
+    if (P.kind == IRK_PC_UNCOUPLED && s > 1) {
+        bool upper_touched = false;
+        for (int R = 0; R < h.nb && !upper_touched; ++R)
+            for (int p = h.rp[R]; p < h.rp[R + 1] && !upper_touched; ++p)
+                for (int u = h.upd_ptr[p]; u < h.upd_ptr[p + 1]; ++u)
+                    if (h.ci[h.upd[2 * u]] > R) upper_touched = true;
+        if (!upper_touched) {
+            P.shared_upper = 1;
+            up0_ptr.push_back(0);
+            for (size_t l = 0; l + 1 < h.up_ptr.size(); ++l) {
+                for (int q = h.up_ptr[l]; q < h.up_ptr[l + 1]; ++q)
+                    if (h.up_rows[q] < T) up0_rows.push_back(h.up_rows[q]);
+                up0_ptr.push_back((int)up0_rows.size());
+            }
+        }
+    }
     P.nb = h.nb;
     P.b = h.b;
     P.nnz = (long long)h.ci.size();
     P.lo_ptr = h.lo_ptr;
     P.up_ptr = h.up_ptr;
+    P.up0_ptr = up0_ptr;
     int rc;
     if ((rc = upload(&P.d_rp, h.rp)) || (rc = upload(&P.d_ci, h.ci)) || (rc = upload(&P.d_diag, h.diag)) ||
         (rc = upload(&P.d_voff, h.voff)) || (rc = upload(&P.d_upd_ptr, h.upd_ptr)) ||
         (rc = upload(&P.d_upd, h.upd)) || (rc = upload(&P.d_lo_rows, h.lo_rows)) ||
-        (rc = upload(&P.d_up_rows, h.up_rows)))
+        (rc = upload(&P.d_up_rows, h.up_rows)) || (P.shared_upper && (rc = upload(&P.d_up0_rows, up0_rows))))
         return rc;
     if (P.element_major) {
         if ((rc = upload(&P.d_rowof, h.rowof))) return rc;
@@ -1238,6 +1390,7 @@ void pc_free(PcSystem &P) {
     cudaFree(P.d_upd);
     cudaFree(P.d_lo_rows);
     cudaFree(P.d_up_rows);
+    cudaFree(P.d_up0_rows);
     cudaFree(P.d_vals);
     cudaFree(P.d_dinv);
     cudaFree(P.d_vals16);
@@ -1259,7 +1412,8 @@ static int factor_impl(irk_ctx *c, double dt) {
         const double *C0 = transformed ? c->Ainv : c->A;
         for (int q = 0; q < s * s; ++q) tab.cm[q] = C0[q];
         k_assemble_elem<C><<<grid_cap(P.nnz * P.b * P.b), 256, 0, c->stream>>>(
-            P.nnz, s, c->m, transformed ? 0 : 1, P.d_rowof, P.d_ci, c->d_J, c->d_M, c->df, tab, dt, (C *)P.d_vals);
+            P.nnz, s, c->m, transformed ? 0 : 1, P.d_rowof, P.d_ci, c->d_J,
+            c->nJ > 1 ? (long long)c->nnzb * c->m * c->m : 0LL, c->d_M, c->df, tab, dt, (C *)P.d_vals);
     } else {
         if (P.kind == IRK_PC_UNCOUPLED) {
             for (int k = 0; k < s; ++k) tab.cm[k * s + k] = c->Ainv[k * s + k] + c->shift[k];
@@ -1281,19 +1435,33 @@ static int factor_impl(irk_ctx *c, double dt) {
     const bool fast = smem4 <= 227 * 1024;
     allow_max_smem((const void *)k_factor_level2<C>);
     allow_max_smem((const void *)k_factor_level<C>);
+    allow_max_smem((const void *)k_factor_diag<C>);
     const int nlev = (int)P.lo_ptr.size() - 1;
+    // inversions in their own small CTAs: every row of level 0 (no lower
+    // entries: nothing to update), and the rows of levels with at least
+    // split_min rows after their products (one more launch per level)
+    const int gjt = std::max(gj_threads(), (b + 31) / 32 * 32);
+    const size_t smem_d = ((size_t)2 * b * b + (size_t)2 * b) * sizeof(C);
     for (int l = 0; l < nlev; ++l) {
         int n = P.lo_ptr[l + 1] - P.lo_ptr[l];
         if (n <= 0) continue;
-        if (fast)
-            k_factor_level2<C><<<n, 256, smem4, c->stream>>>(P.d_lo_rows + P.lo_ptr[l], b, P.d_rp, P.d_ci,
-                                                             P.d_diag, P.d_upd_ptr, P.d_upd, (C *)P.d_vals,
-                                                             (C *)P.d_dinv, c->d_err);
-        else
+        const int *lrows = P.d_lo_rows + P.lo_ptr[l];
+        if (fast) {
+            const bool split = l == 0 || n >= gj_split_min();
+            if (l > 0)
+                k_factor_level2<C><<<n, 256, smem4, c->stream>>>(lrows, b, P.d_rp, P.d_ci, P.d_diag, P.d_upd_ptr,
+                                                                 P.d_upd, (C *)P.d_vals, (C *)P.d_dinv, c->d_err,
+                                                                 split ? 0 : 1);
+            if (split) {
+                k_factor_diag<C><<<n, gjt, smem_d, c->stream>>>(lrows, b, P.d_diag, (const C *)P.d_vals,
+                                                                (C *)P.d_dinv, c->d_err);
+                c->launches++;
+            }
+        } else
             k_factor_level<C><<<n, 256, smem, c->stream>>>(P.d_lo_rows + P.lo_ptr[l], b, P.d_rp, P.d_ci,
                                                            P.d_diag, P.d_upd_ptr, P.d_upd, (C *)P.d_vals,
                                                            (C *)P.d_dinv, c->d_err);
-        c->launches++;
+        if (!fast || l > 0) c->launches++;
     }
     if (c->fprec == IRK_FACTOR_BF16) {
         const long long bb = (long long)b * b;
@@ -1362,6 +1530,20 @@ static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F
         c->launches++;
     }
     const size_t smem = (size_t)groups * b * sizeof(C);
+    const int s = c->s;
+    if (P.shared_upper && s >= 2 && s <= 4 && getenv("IRK_NO_SHARED_UPPER") == nullptr) {
+        auto kern = s == 2 ? k_sweep_bwd_shared<AR, C, F, 2>
+                           : (s == 3 ? k_sweep_bwd_shared<AR, C, F, 3> : k_sweep_bwd_shared<AR, C, F, 4>);
+        const int nup0 = (int)P.up0_ptr.size() - 1;
+        for (int l = 0; l < nup0; ++l) {
+            int n = P.up0_ptr[l + 1] - P.up0_ptr[l];
+            if (n <= 0) continue;
+            kern<<<(n + groups - 1) / groups, threads, smem * s, c->stream>>>(
+                P.d_up0_rows + P.up0_ptr[l], n, b, c->T, P.d_rp, P.d_ci, P.d_voff, vals, dinv, y, z);
+            c->launches++;
+        }
+        return cuda_status(cudaGetLastError());
+    }
     const int nup = (int)P.up_ptr.size() - 1;
     for (int l = 0; l < nup; ++l) {
         int n = P.up_ptr[l + 1] - P.up_ptr[l];
@@ -1545,13 +1727,13 @@ int ilu_factor_level(cudaStream_t st, int fprec, const int *rows, int nrows, int
         if (smem4 > 227 * 1024) return IRK_ERR_INVALID;
         allow_max_smem((const void *)k_factor_level2<double>);
         k_factor_level2<double><<<nrows, 256, smem4, st>>>(rows, b, rp, ci, diag, upd_ptr, upd, (double *)vals,
-                                                           (double *)dinv, err);
+                                                           (double *)dinv, err, 1);
     } else {
         const size_t smem4 = (size_t)b * b * 4 * 4 + (size_t)2 * b * 4;
         if (smem4 > 227 * 1024) return IRK_ERR_INVALID;
         allow_max_smem((const void *)k_factor_level2<float>);
         k_factor_level2<float><<<nrows, 256, smem4, st>>>(rows, b, rp, ci, diag, upd_ptr, upd, (float *)vals,
-                                                          (float *)dinv, err);
+                                                          (float *)dinv, err, 1);
     }
     return cuda_status(cudaGetLastError());
 }

@@ -6,6 +6,8 @@
 // order of work, and the last CTA to finish (ticket counter) sums the
 // partials in index order with a fixed tree.  No floating-point atomics, so
 // the same input gives bit-identical results.
+#include <stdlib.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -194,8 +196,8 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, int *err, int *s_ok) {
 // per-CTA partials are summed in index order by every CTA (identical values
 // everywhere, deterministic), in a buffer alternating between steps so that a
 // CTA already in the next step never overwrites partials still being read.
-template <class AR>
-__global__ void __launch_bounds__(256) k_arnoldi(long long N, int j, int R, vec8 *w, const vec8 *V, Scal *slots,
+template <class AR, int NT>
+__global__ void __launch_bounds__(NT) k_arnoldi(long long N, int j, int R, vec8 *w, const vec8 *V, Scal *slots,
                                                  double *H, double *cs, double *sn, double *g, double *est,
                                                  vec8 *part, unsigned *bar, int *err) {
     typedef typename AR::val val;
@@ -355,35 +357,48 @@ int launch_givens(irk_ctx *c, int j, int restart) {
     return cuda_status(cudaGetLastError());
 }
 
-// Grid of k_arnoldi: every CTA resident (cooperative launch), as many as fit
-// (streaming needs the loads of every resident thread in flight), at most
-// half of IRK_PART_SLOTS (the partial buffer holds two steps); 0 when the
-// device has no cooperative launch.
-static int arnoldi_grid(irk_ctx *c) {
+// Launch shape of k_arnoldi: every CTA resident (cooperative launch).  Few
+// large CTAs keep the grid barrier (one atomic per CTA on one counter) and
+// the all-CTA reduction (every CTA reads every partial) short: one
+// 1024-thread CTA per SM by default; IRK_ARNOLDI_THREADS=256 selects
+// 256-thread CTAs, as many as fit.  At most IRK_PART_SLOTS / 2 CTAs (the
+// partial buffer holds two steps).  grid 0: no cooperative launch.
+struct ArnoldiShape {
+    int grid = -1, threads = 0;
+};
+
+template <class AR>
+static ArnoldiShape arnoldi_shape_for() {
+    ArnoldiShape sh;
+    int dev = 0, coop = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const char *env = getenv("IRK_ARNOLDI_THREADS");
+    sh.threads = (env && atoi(env) == 256) ? 256 : 1024;
+    if (sh.threads == 256)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<AR, 256>, 256, 0);
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<AR, 1024>, 1024, 0);
+    sh.grid = (coop && per_sm > 0) ? std::min(sms * per_sm, IRK_PART_SLOTS / 2) : 0;
+    return sh;
+}
+
+static ArnoldiShape arnoldi_shape(irk_ctx *c) {
     static std::mutex mu;
-    static int cached[2] = {-1, -1};
+    static ArnoldiShape cached[2];
     std::lock_guard<std::mutex> lk(mu);
-    int &gsz = cached[c->df ? 1 : 0];
-    if (gsz < 0) {
-        int dev = 0, coop = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (c->df)
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<ArDF>, 256, 0);
-        else
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<ArF64>, 256, 0);
-        gsz = coop ? sms * per_sm : 0;
-    }
-    return std::min(gsz, IRK_PART_SLOTS / 2);
+    ArnoldiShape &sh = cached[c->df ? 1 : 0];
+    if (sh.grid < 0) sh = c->df ? arnoldi_shape_for<ArDF>() : arnoldi_shape_for<ArF64>();
+    return sh;
 }
 
 // The whole Arnoldi step j (orthogonalisation, normalisation, Givens) in one
 // launch; returns IRK_ERR_INVALID when the device cannot launch it (the
 // caller then issues the step as separate launches).
 int launch_arnoldi(irk_ctx *c, int j, int restart, vec8 *w) {
-    const int grid = arnoldi_grid(c);
-    if (grid <= 0) return IRK_ERR_INVALID;
+    const ArnoldiShape sh = arnoldi_shape(c);
+    if (sh.grid <= 0) return IRK_ERR_INVALID;
     long long N = c->N;
     int jj = j, R = restart;
     const vec8 *V = c->d_V;
@@ -392,11 +407,12 @@ int launch_arnoldi(irk_ctx *c, int j, int restart, vec8 *w) {
     vec8 *part = reinterpret_cast<vec8 *>(c->d_part);
     void *args[] = {&N, &jj, &R, &w, &V, &slots, &c->d_H, &c->d_cs, &c->d_sn, &c->d_g, &est, &part, &c->d_gbar,
                     &c->d_err};
-    cudaError_t e;
+    const void *fn;
     if (c->df)
-        e = cudaLaunchCooperativeKernel((const void *)k_arnoldi<ArDF>, grid, 256, args, 0, c->stream);
+        fn = sh.threads == 256 ? (const void *)k_arnoldi<ArDF, 256> : (const void *)k_arnoldi<ArDF, 1024>;
     else
-        e = cudaLaunchCooperativeKernel((const void *)k_arnoldi<ArF64>, grid, 256, args, 0, c->stream);
+        fn = sh.threads == 256 ? (const void *)k_arnoldi<ArF64, 256> : (const void *)k_arnoldi<ArF64, 1024>;
+    const cudaError_t e = cudaLaunchCooperativeKernel(fn, sh.grid, sh.threads, args, 0, c->stream);
     c->launches++;
     return cuda_status(e);
 }

@@ -40,7 +40,7 @@ class Options(ctypes.Structure):
                 ("formulation", ctypes.c_int), ("shift", ctypes.POINTER(ctypes.c_double)),
                 ("stream", ctypes.c_void_p), ("timing", ctypes.c_int), ("sweep", ctypes.c_int),
                 ("ordering", ctypes.c_int), ("partitions", ctypes.c_int),
-                ("partition", ctypes.POINTER(ctypes.c_int32))]
+                ("partition", ctypes.POINTER(ctypes.c_int32)), ("stage_jacobians", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -130,7 +130,7 @@ class Solver:
     def __init__(self, s, T, m, row_ptr, col_idx, J, M, A=None, precond="uncoupled",
                  factor_prec="fp64", krylov="fp64", formulation="transformed", restart=30,
                  max_iter=3000, shift=None, stream=None, timing=False, sweep="auto",
-                 ordering="natural", partitions=0, partition=None):
+                 ordering="natural", partitions=0, partition=None, stage_jacobians=False):
         lib = load()
         self._lib = lib
         self.s, self.T, self.m = int(s), int(T), int(m)
@@ -153,6 +153,7 @@ class Solver:
         opt.sweep = {"auto": 0, "levels": 1}[sweep]
         opt.ordering = {"natural": 0, "multicolor": 1}[ordering]
         opt.partitions = int(partitions)
+        opt.stage_jacobians = 1 if stage_jacobians else 0
         self._part = None
         if partition is not None:
             self._part = np.ascontiguousarray(partition, dtype=np.int32)

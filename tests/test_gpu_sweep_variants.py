@@ -1,0 +1,57 @@
+"""Backward-sweep variants of the uncoupled preconditioner (Sec. 4.3.2).
+
+* Where no factor update reaches an upper block (every generated mesh: no
+  element has two mutually adjacent neighbours), each stage's upper blocks
+  are -dt J_ij and the backward sweep reads one copy for all stages; the
+  application is bitwise equal to the per-stage sweep
+  (IRK_NO_SHARED_UPPER=1 forces the latter).
+* On a pattern with mutually adjacent elements the factor does modify upper
+  blocks; the library keeps the per-stage sweep there, and the FP64
+  application still matches the oracle.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1701_07181_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def _irk():
+    from paper_1701_07181_gb300 import irk
+    return irk
+
+
+@pytest.mark.parametrize("fprec,krylov", [("fp32", "df64"), ("fp64", "fp64"), ("bf16", "df64")])
+@pytest.mark.parametrize("kind,s,m", [("2d", 3, 40), ("3d", 2, 20), ("2d", 4, 12)])
+def test_shared_upper_sweep_is_bitwise_equal(monkeypatch, fprec, krylov, kind, s, m):
+    irk = _irk()
+    nb = inputs.mesh_2d_periodic(9, 7) if kind == "2d" else inputs.mesh_3d_periodic(3, 3, 4)
+    P = inputs.make_problem(nb, m, s, 0.3, 4.0, seed=2)
+    V = np.random.default_rng(8).standard_normal(P.s * P.T * P.m)
+    out = []
+    for off in ("", "1"):
+        if off:
+            monkeypatch.setenv("IRK_NO_SHARED_UPPER", "1")
+        with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec=fprec, krylov=krylov,
+                        sweep="levels", ordering="multicolor") as S:
+            S.factor(0.3)
+            out.append(S.apply_precond(V))
+    np.testing.assert_array_equal(out[0], out[1])
+
+
+def test_mutual_neighbours_fall_back_and_match_oracle():
+    irk = _irk()
+    # 0-1-2 and 1-2-4 are triangles of the element graph
+    nbrs = [[1, 2], [0, 2, 3], [0, 1, 4], [1, 4], [2, 3]]
+    P = inputs.make_problem(nbrs, 6, 3, 0.4, 4.0, seed=5)
+    V = np.random.default_rng(1).standard_normal(P.s * P.T * P.m)
+    ref = oracle.Problem(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M).precond_apply(V, 0.4)
+    for sweep in ("levels", "auto"):
+        with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec="fp64", krylov="fp64",
+                        sweep=sweep) as S:
+            S.factor(0.4)
+            z = S.apply_precond(V)
+        assert np.linalg.norm(z - ref) <= 1e-11 * np.linalg.norm(ref)
