@@ -66,11 +66,22 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def traffic_record(phase):
-    """DRAM bytes of one unit of a phase (matvec: one launch; precond_sweeps:
-    one application; factorization: one factorisation) from the committed ncu
-    summary, or None when absent or taken on a different source of the
-    kernels."""
+def measured_bf16():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except Exception:
+        return None
+
+
+MEASURED_BF16 = measured_bf16()
+
+
+def traffic_record(kernel):
+    """DRAM bytes of one unit of a kernel (matvec: one launch; sweep_fwd /
+    sweep_bwd: the launches of one application; factor_*: the launches of one
+    factorisation) from the committed ncu summary, or None when absent or
+    taken on a different source of the kernel."""
     path = os.path.join(ROOT, "profiles", "dram_traffic_c1.txt")
     if not os.path.exists(path):
         return None
@@ -228,7 +239,7 @@ def dirk_comparison(P, dev, rp, ci, J, M, dt=0.1, reps=3):
     multiplications = iterations x s (coupled system) or the sum of the
     stages' iterations (DIRK)."""
     import torch
-    from paper_1701_07181_gb300 import tableaux
+    from paper_1701_07181_gb300 import irk, tableaux
     T, m = P.T, P.m
     u0 = torch.as_tensor(np.random.default_rng(17).standard_normal(T * m), device=dev)
     # J u0 by block gather (input preparation, untimed)
@@ -277,10 +288,64 @@ def dirk_comparison(P, dev, rp, ci, J, M, dt=0.1, reps=3):
     return out
 
 
+def kernel_rooflines(P, r, acc, hbm_peak, peak_kind):
+    """Per-kernel measured time (CUDA events, irk_options.timing) over the
+    timed solves, algorithmic bytes or flops per unit, and the roofline of
+    the kernel with the largest total time."""
+    s, T, m = P.s, P.T, P.m
+    n = T * m
+    mm = m * m
+    nnzb = P.nnzb
+    lower = (nnzb - T) // 2  # lower blocks per stage (symmetric pattern)
+    alu_peak = 152 * 128 * 2 * 2.070e9 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
+    tf32_peak = MEASURED_BF16 * 1.1 / 2.25 if MEASURED_BF16 else 1100.0  # nominal tf32 / bf16 ratio
+    napp = max(1, acc["n_precond"])
+    nfac = max(1, len(acc["iters"]))
+    rows = {
+        # name: (total ms, units, algorithmic amount per unit, kind)
+        "matvec": (acc["matvec_ms"], acc["n_matvec"], 8 * (r + 1) * mm * T + 8 * mm * T + 16 * s * n, "hbm"),
+        "sweep_fwd": (acc.get("sweep_fwd_ms", 0.0), napp, 4 * s * lower * mm + 8 * s * n + 4 * s * n, "hbm"),
+        "sweep_bwd": (acc.get("sweep_bwd_ms", 0.0), napp, 4 * lower * mm + 4 * s * mm * T + 16 * s * n, "hbm"),
+        "factor_assemble": (acc.get("factor_assemble_ms", 0.0), nfac,
+                            8 * nnzb * mm + 8 * mm * T + 4 * s * nnzb * mm, "hbm"),
+        "factor_products": (acc.get("factor_products_ms", 0.0), nfac, 4.0 * s * lower * m ** 3, "tensor"),
+        "factor_inverse": (acc.get("factor_inverse_ms", 0.0), nfac, 2.0 * s * T * m ** 3, "alu"),
+    }
+    kernels = {}
+    for name, (tot, units, amount, kind) in rows.items():
+        avg = tot / max(1, units)
+        entry = {"total_ms": tot, "units": units, "avg_ms": avg}
+        if kind == "hbm":
+            entry["alg_bytes"] = amount
+            entry["achieved_gbs"] = amount / (avg * 1e6) if avg > 0 else None
+        else:
+            entry["alg_flops"] = amount
+            entry["achieved_tflops"] = amount / (avg * 1e9) if avg > 0 else None
+        kernels[name] = entry
+    kernels["arnoldi_total_ms"] = acc["ortho_ms"]
+    kernels["factor_total_ms"] = acc["factor_ms"]
+    kernels["precond_total_ms"] = acc["precond_ms"]
+    dominant = max(rows, key=lambda k: rows[k][0])
+    dk, kind = kernels[dominant], rows[dominant][3]
+    if kind == "hbm":
+        roofline = {"bound": "hbm", "kernel": dominant, "achieved": dk["achieved_gbs"], "peak": hbm_peak,
+                    "unit": "GB/s", "frac": dk["achieved_gbs"] / hbm_peak if dk["achieved_gbs"] else None,
+                    "peak_source": peak_kind + " hbm_gbs", "traffic": traffic_record(dominant)}
+    else:
+        pk = tf32_peak if kind == "tensor" else alu_peak
+        src = ("measured bf16 x nominal tf32/bf16 ratio (1.1/2.25)" if kind == "tensor" else
+               "FP32 CUDA-core peak from unit counts and max clock (152 x 128 x 2 x 2.07 GHz)")
+        roofline = {"bound": kind if kind == "alu" else "tensor", "kernel": dominant,
+                    "achieved": dk["achieved_tflops"], "peak": pk, "unit": "TFLOP/s",
+                    "frac": dk["achieved_tflops"] / pk if dk["achieved_tflops"] else None, "peak_source": src,
+                    "traffic": traffic_record(dominant)}
+    return roofline, kernels
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -321,8 +386,9 @@ def main():
                 st = solver.stats()
                 acc["launches"] += st["kernel_launches"]
                 acc["iters"].append(it)
-                for k in ("matvec_ms", "precond_ms", "ortho_ms", "factor_ms", "solve_ms"):
-                    acc[k] += st[k]
+                for k in ("matvec_ms", "precond_ms", "ortho_ms", "factor_ms", "solve_ms", "factor_assemble_ms",
+                          "factor_products_ms", "factor_inverse_ms", "sweep_fwd_ms", "sweep_bwd_ms"):
+                    acc[k] = acc.get(k, 0.0) + st[k]
                 for k in ("n_matvec", "n_precond", "n_ortho"):
                     acc[k] += st[k]
 
@@ -409,40 +475,8 @@ def main():
             dist.destroy_process_group()
         return 0
 
-    k1_bytes, k3_bytes = algorithmic_bytes(P.T, P.m, r, P.s)
     peak, peak_kind = peaks()
-    mv_avg = acc["matvec_ms"] / max(1, acc["n_matvec"])
-    pc_avg = acc["precond_ms"] / max(1, acc["n_precond"])
-    n_fac = len(acc["iters"])
-    fac_avg = acc["factor_ms"] / max(1, n_fac)
-    fac_flops = P.s * (2.0 / 3.0 + 2.0 * r) * P.m ** 3 * P.T  # LU of D + two products per lower block
-    # FP32 CUDA-core peak: 152 SMs x 128 lanes x 2 flops x max SM clock
-    alu_peak = 152 * 128 * 2 * 2.070e9 / 1e12
-    kernels = {
-        "matvec": {"avg_ms": mv_avg, "launches": acc["n_matvec"], "alg_bytes": k1_bytes,
-                   "achieved_gbs": k1_bytes / (mv_avg * 1e6) if mv_avg > 0 else None,
-                   "total_ms": acc["matvec_ms"]},
-        "precond_sweeps": {"avg_ms": pc_avg, "applications": acc["n_precond"], "alg_bytes": k3_bytes,
-                           "achieved_gbs": k3_bytes / (pc_avg * 1e6) if pc_avg > 0 else None,
-                           "total_ms": acc["precond_ms"]},
-        "factorization": {"avg_ms": fac_avg, "count": n_fac, "alg_flops": fac_flops,
-                          "achieved_tflops": fac_flops / (fac_avg * 1e9) if fac_avg > 0 else None,
-                          "total_ms": acc["factor_ms"]},
-        "gram_schmidt_total_ms": acc["ortho_ms"],
-    }
-    dominant = max(("precond_sweeps", "matvec", "factorization"), key=lambda k: kernels[k]["total_ms"])
-    dk = kernels[dominant]
-    if dominant == "factorization":
-        achieved = dk["achieved_tflops"]
-        roofline = {"bound": "alu", "kernel": dominant, "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": achieved / alu_peak if achieved else None,
-                    "peak_source": "FP32 CUDA-core peak from unit counts and max clock (152 x 128 x 2 x 2.07 GHz)",
-                    "traffic": traffic_record("factorization")}
-    else:
-        achieved = dk["achieved_gbs"]
-        roofline = {"bound": "hbm", "kernel": dominant, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak if achieved else None, "peak_source": peak_kind + " hbm_gbs",
-                    "traffic": traffic_record(dominant)}
+    roofline, kernels = kernel_rooflines(P, r, acc, peak, peak_kind)
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "df64 Krylov / f32 factors",

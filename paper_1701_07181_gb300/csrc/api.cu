@@ -176,8 +176,12 @@ int load_values(irk_ctx *c, const double *J, const double *M, int mem_space) {
     return rc;
 }
 
+}  // namespace
+
 // Phase timing: tmark_begin / tmark_end record a pair of events around a
-// phase of kind 0 (operator product), 1 (preconditioner), 2 (Gram-Schmidt).
+// phase of kind 0 (operator product), 1 (preconditioner), 2 (Gram-Schmidt),
+// 3 (factor assembly), 4 (factor block products), 5 (factor inverses),
+// 6 (forward sweep), 7 (backward sweep).
 int tmark_begin(irk_ctx *c) {
     if (!c->opt.timing) return -1;
     if (c->tused + 2 > (int)c->tev.size()) {
@@ -200,8 +204,11 @@ void tmark_end(irk_ctx *c, int slot, int kind) {
     c->tkind[slot / 2] = kind;
 }
 
+namespace {
+
 void tcollect(irk_ctx *c) {
     c->stats.matvec_ms = c->stats.precond_ms = c->stats.ortho_ms = 0.0;
+    c->stats.sweep_fwd_ms = c->stats.sweep_bwd_ms = 0.0;
     c->stats.n_matvec = c->stats.n_precond = c->stats.n_ortho = 0;
     for (int slot = 0; slot < c->tused; slot += 2) {
         float ms = 0.f;
@@ -209,7 +216,25 @@ void tcollect(irk_ctx *c) {
         switch (c->tkind[slot / 2]) {
             case 0: c->stats.matvec_ms += ms; c->stats.n_matvec++; break;
             case 1: c->stats.precond_ms += ms; c->stats.n_precond++; break;
+            case 6: c->stats.sweep_fwd_ms += ms; break;
+            case 7: c->stats.sweep_bwd_ms += ms; break;
             default: c->stats.ortho_ms += ms; c->stats.n_ortho++; break;
+        }
+    }
+    c->tused = 0;
+}
+
+// the factorisation's marks (kinds 3-5), collected after its synchronisation
+static void tcollect_factor(irk_ctx *c) {
+    c->stats.factor_assemble_ms = c->stats.factor_products_ms = c->stats.factor_inverse_ms = 0.0;
+    for (int slot = 0; slot < c->tused; slot += 2) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->tev[slot], c->tev[slot + 1]);
+        switch (c->tkind[slot / 2]) {
+            case 3: c->stats.factor_assemble_ms += ms; break;
+            case 4: c->stats.factor_products_ms += ms; break;
+            case 5: c->stats.factor_inverse_ms += ms; break;
+            default: break;
         }
     }
     c->tused = 0;
@@ -444,12 +469,14 @@ int irk_factor(irk_ctx *c, double dt) {
     cudaEventCreate(&e1);
     long long l0 = c->launches;
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    c->tused = 0;
     cudaEventRecord(e0, c->stream);
     int rc = pc_factor(c, dt);
     cudaEventRecord(e1, c->stream);
     if (rc == IRK_OK) rc = sync_err(c);
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    tcollect_factor(c);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->stats.factor_ms = ms;

@@ -117,6 +117,9 @@ int launch_jacobian(irk_ctx *c, const vec8 *x, vec8 *y);
 #define IRK_FORM_JACOBIAN 2
 // raise a kernel's dynamic shared-memory limit to the device maximum (once)
 int irk_allow_max_smem(const void *func);
+// phase timing marks (api.cu): no-ops unless irk_options.timing
+int tmark_begin(irk_ctx *c);
+void tmark_end(irk_ctx *c, int slot, int kind);
 // stage-major binary64 <-> element-interleaved vec8
 int launch_to_internal(irk_ctx *c, const double *src, vec8 *dst);
 int launch_to_external(irk_ctx *c, const vec8 *src, double *dst);

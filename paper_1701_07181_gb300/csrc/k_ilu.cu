@@ -137,6 +137,39 @@ __global__ void __launch_bounds__(256) k_assemble(long long nnz, int m, const As
     }
 }
 
+// Uncoupled kind with one shared J: the s stage systems list their blocks
+// in the same order (stage k's entry q0 + k * per_stage has stage 0's J and
+// M blocks), so one CTA reads a J block (and the mass block on the
+// diagonal) once and writes all s assembled blocks d_k M - dt J, each with
+// k_assemble's arithmetic.  Entries are read from stage 0's part of the table.
+template <class C>
+__global__ void __launch_bounds__(256) k_assemble_stages(long long per_stage, int s, int m, const AsmEntry *ent,
+                                                         const vec8 *J, const vec8 *M, int df, AsmTables tab,
+                                                         C *vals) {
+    const int mm = m * m;
+    for (long long q = blockIdx.x; q < per_stage; q += gridDim.x) {
+        const AsmEntry a = ent[q];
+        const vec8 *Mb = a.mi >= 0 ? M + (long long)a.mi * mm : nullptr;
+        const vec8 *Jb = a.jp >= 0 ? J + (long long)a.jp * mm : nullptr;
+        const C cj = Jb ? (C)tab.cj[a.cj_id] : C(0);
+        C cmk[IRK_MAX_S];
+#pragma unroll
+        for (int k = 0; k < IRK_MAX_S; ++k) cmk[k] = (Mb && k < s) ? (C)tab.cm[k * s + k] : C(0);
+        for (int r = threadIdx.x; r < mm; r += blockDim.x) {
+            const C mv = Mb ? CT<C>::from_store(Mb[r], df) : C(0);
+            const C jv = Jb ? CT<C>::from_store(Jb[r], df) : C(0);
+#pragma unroll
+            for (int k = 0; k < IRK_MAX_S; ++k) {
+                if (k >= s) break;
+                C v = C(0);
+                if (Mb) v += cmk[k] * mv;
+                if (Jb) v += cj * jv;
+                vals[(q + k * per_stage) * mm + r] = v;
+            }
+        }
+    }
+}
+
 // Element-major assembly: one (s m) x (s m) block per J block p, entry
 // ((k,a),(l,c)) at column-major index (l m + c) * sm + (k m + a).
 //   form 0: C_kl M_i[a][c] [diag] - dt [k==l] J_p[a][c]
@@ -675,6 +708,121 @@ __device__ __forceinline__ C block_col_dot(const F *B, const C *x, int b) {
         }
     }
     return s0 + s1;
+}
+
+// ---------------------------------------------------------------------------
+// Gauss-Jordan inverses with the rows in registers (block sizes known at
+// compile time).  One CTA of round_up(B, 32) threads per block; thread r
+// keeps row r of the block in registers and the elimination is fully
+// unrolled.  Pivoting is partial and implicit: at step k the pivot is the
+// row not yet used as a pivot with the largest |A[r][k]| (lowest row on
+// ties), found by a warp max of (|value|, row) keys plus a max over the
+// warps' keys; the pivot row is scaled and broadcast through shared memory
+// and every other row eliminates column k with it (in-place form: column k
+// takes the inverse's column).  The rows are never swapped; with piv[c] the
+// pivot row of step c, the inverse is inv[k][piv[c]] = S[piv[k]][c], so the
+// thread whose row was step k's pivot writes inverse row k.  Two barriers
+// per step (pivot keys, pivot row), each over one or two warps.
+template <class C>
+__device__ __forceinline__ unsigned long long gjr_key(C v, int r);
+template <>
+__device__ __forceinline__ unsigned long long gjr_key<float>(float v, int r) {
+    const unsigned bits = v == v ? __float_as_uint(fabsf(v)) : 0u;  // NaN: magnitude 0
+    return ((unsigned long long)bits << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)r);
+}
+template <>
+__device__ __forceinline__ unsigned long long gjr_key<double>(double v, int r) {
+    // magnitude's top 57 bits (rows < 128): values equal to 2^-45 relative tie
+    const unsigned long long bits = v == v ? (unsigned long long)__double_as_longlong(fabs(v)) : 0ull;
+    return (bits & ~127ull) | (unsigned long long)(127 - r);
+}
+template <class C>
+__device__ __forceinline__ void gjr_decode(unsigned long long key, int &row, C &mag);
+template <>
+__device__ __forceinline__ void gjr_decode<float>(unsigned long long key, int &row, float &mag) {
+    row = (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
+    mag = __uint_as_float((unsigned)(key >> 32));
+}
+template <>
+__device__ __forceinline__ void gjr_decode<double>(unsigned long long key, int &row, double &mag) {
+    row = 127 - (int)(key & 127ull);
+    mag = __longlong_as_double((long long)(key & ~127ull));
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, v, d);
+        v = o > v ? o : v;
+    }
+    return v;
+}
+
+template <class C, int B>
+__global__ void __launch_bounds__((B + 31) / 32 * 32) k_factor_diag_rows(const int *rows, const int *diag,
+                                                                          const C *vals, C *dinv, int *err) {
+    constexpr int NW = (B + 31) / 32;
+    __shared__ C s_prow[2][B];
+    __shared__ unsigned long long s_key[2][NW];
+    __shared__ int s_piv[B];
+    const int r = threadIdx.x, lane = r & 31, w = r >> 5;
+    const bool act = r < B;
+    const int R = rows[blockIdx.x];
+    const C *D = vals + (long long)diag[R] * (B * B);
+    C A[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) A[c] = act ? D[c * B + r] : C(0);
+    bool used = !act;
+    int mystep = 0;
+    bool bad = false;
+    {
+        const unsigned long long key = warp_max_u64(used ? 0ull : gjr_key<C>(A[0], r));
+        if (lane == 0) s_key[0][w] = key;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < B; ++k) {
+        const int buf = k & 1;
+        unsigned long long kmax = 0ull;
+#pragma unroll
+        for (int q = 0; q < NW; ++q) kmax = s_key[buf][q] > kmax ? s_key[buf][q] : kmax;
+        int p;
+        C mag;
+        gjr_decode<C>(kmax, p, mag);
+        const bool zero = !(mag > C(0));
+        bad |= zero;
+        if (r == p) {
+            const C pinv = C(1) / (zero ? C(1) : A[k]);
+#pragma unroll
+            for (int c = 0; c < B; ++c) {
+                const C v = c == k ? pinv : A[c] * pinv;
+                s_prow[buf][c] = v;
+                A[c] = v;
+            }
+            used = true;
+            mystep = k;
+            s_piv[k] = r;
+        }
+        __syncthreads();
+        if (act && r != p) {
+            const C f = A[k];
+#pragma unroll
+            for (int c = 0; c < B; ++c)
+                if (c != k) A[c] = fma_rn(-f, s_prow[buf][c], A[c]);
+            A[k] = -f * s_prow[buf][k];
+        }
+        if (k + 1 < B) {
+            const unsigned long long key = warp_max_u64(used ? 0ull : gjr_key<C>(A[k + 1], r));
+            if (lane == 0) s_key[buf ^ 1][w] = key;
+        }
+        __syncthreads();
+    }
+    if (act) {
+        C *out = dinv + (long long)R * (B * B);
+#pragma unroll
+        for (int c = 0; c < B; ++c) out[s_piv[c] * B + mystep] = A[c];
+    }
+    if (bad && r == 0) atomicOr(err, IRK_DEV_ERR_SINGULAR);
 }
 
 // ---------------------------------------------------------------------------
@@ -1401,6 +1549,23 @@ void pc_free(PcSystem &P) {
     P = PcSystem();
 }
 
+// The register-row inversion for the block sizes it is compiled for
+// (IRK_GJ_ROWS=0 selects the shared-memory kernel); false otherwise.
+template <class C>
+static bool launch_diag_rows(cudaStream_t st, int n, int b, const int *rows, const int *diag, const C *vals, C *dinv,
+                             int *err) {
+    static const bool on = env_int("IRK_GJ_ROWS", 1) != 0;
+    if (!on) return false;
+    switch (b) {
+        case 12: k_factor_diag_rows<C, 12><<<n, 32, 0, st>>>(rows, diag, vals, dinv, err); return true;
+        case 20: k_factor_diag_rows<C, 20><<<n, 32, 0, st>>>(rows, diag, vals, dinv, err); return true;
+        case 24: k_factor_diag_rows<C, 24><<<n, 32, 0, st>>>(rows, diag, vals, dinv, err); return true;
+        case 40: k_factor_diag_rows<C, 40><<<n, 64, 0, st>>>(rows, diag, vals, dinv, err); return true;
+        case 50: k_factor_diag_rows<C, 50><<<n, 64, 0, st>>>(rows, diag, vals, dinv, err); return true;
+        default: return false;
+    }
+}
+
 template <class C>
 static int factor_impl(irk_ctx *c, double dt) {
     PcSystem &P = c->pc;
@@ -1408,6 +1573,7 @@ static int factor_impl(irk_ctx *c, double dt) {
     AsmTables tab;
     memset(&tab, 0, sizeof(tab));
     const bool transformed = c->opt.formulation == IRK_TRANSFORMED;
+    int tm = tmark_begin(c);
     if (P.element_major) {
         const double *C0 = transformed ? c->Ainv : c->A;
         for (int q = 0; q < s * s; ++q) tab.cm[q] = C0[q];
@@ -1425,10 +1591,15 @@ static int factor_impl(irk_ctx *c, double dt) {
             tab.cm[0] = 1.0;
             for (int q = 0; q < s * s; ++q) tab.cj[q] = -dt * c->A[q];
         }
-        k_assemble<C><<<grid_cap(P.nnz * 256), 256, 0, c->stream>>>(P.nnz, c->m, P.d_asm, c->d_J, c->d_M,
-                                                                           c->df, tab, (C *)P.d_vals);
+        if (P.kind == IRK_PC_UNCOUPLED && c->nJ == 1 && P.nnz % s == 0)
+            k_assemble_stages<C><<<grid_cap(P.nnz / s * 256), 256, 0, c->stream>>>(
+                P.nnz / s, s, c->m, P.d_asm, c->d_J, c->d_M, c->df, tab, (C *)P.d_vals);
+        else
+            k_assemble<C><<<grid_cap(P.nnz * 256), 256, 0, c->stream>>>(P.nnz, c->m, P.d_asm, c->d_J, c->d_M,
+                                                                       c->df, tab, (C *)P.d_vals);
     }
     c->launches++;
+    tmark_end(c, tm, 3);
     const int b = P.b;
     const size_t smem = (size_t)b * b * sizeof(C) * 2 + (size_t)b * sizeof(C);
     const size_t smem4 = (size_t)b * b * sizeof(C) * 4 + (size_t)2 * b * sizeof(C);
@@ -1448,19 +1619,29 @@ static int factor_impl(irk_ctx *c, double dt) {
         const int *lrows = P.d_lo_rows + P.lo_ptr[l];
         if (fast) {
             const bool split = l == 0 || n >= gj_split_min();
-            if (l > 0)
+            if (l > 0) {
+                tm = tmark_begin(c);
                 k_factor_level2<C><<<n, 256, smem4, c->stream>>>(lrows, b, P.d_rp, P.d_ci, P.d_diag, P.d_upd_ptr,
                                                                  P.d_upd, (C *)P.d_vals, (C *)P.d_dinv, c->d_err,
                                                                  split ? 0 : 1);
+                tmark_end(c, tm, 4);
+            }
             if (split) {
-                k_factor_diag<C><<<n, gjt, smem_d, c->stream>>>(lrows, b, P.d_diag, (const C *)P.d_vals,
-                                                                (C *)P.d_dinv, c->d_err);
+                tm = tmark_begin(c);
+                if (!launch_diag_rows<C>(c->stream, n, b, lrows, P.d_diag, (const C *)P.d_vals, (C *)P.d_dinv,
+                                         c->d_err))
+                    k_factor_diag<C><<<n, gjt, smem_d, c->stream>>>(lrows, b, P.d_diag, (const C *)P.d_vals,
+                                                                    (C *)P.d_dinv, c->d_err);
+                tmark_end(c, tm, 5);
                 c->launches++;
             }
-        } else
+        } else {
+            tm = tmark_begin(c);
             k_factor_level<C><<<n, 256, smem, c->stream>>>(P.d_lo_rows + P.lo_ptr[l], b, P.d_rp, P.d_ci,
                                                            P.d_diag, P.d_upd_ptr, P.d_upd, (C *)P.d_vals,
                                                            (C *)P.d_dinv, c->d_err);
+            tmark_end(c, tm, 4);
+        }
         if (!fast || l > 0) c->launches++;
     }
     if (c->fprec == IRK_FACTOR_BF16) {
@@ -1522,6 +1703,7 @@ static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F
     const int threads = (groups * b + 31) / 32 * 32;
     C *y = (C *)P.d_y;
     const int nlo = (int)P.lo_ptr.size() - 1;
+    int tm = tmark_begin(c);
     for (int l = 0; l < nlo; ++l) {
         int n = P.lo_ptr[l + 1] - P.lo_ptr[l];
         if (n <= 0) continue;
@@ -1529,6 +1711,8 @@ static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F
             P.d_lo_rows + P.lo_ptr[l], n, b, P.d_rp, P.d_ci, P.d_voff, vals, v, y);
         c->launches++;
     }
+    tmark_end(c, tm, 6);
+    tm = tmark_begin(c);
     const size_t smem = (size_t)groups * b * sizeof(C);
     const int s = c->s;
     if (P.shared_upper && s >= 2 && s <= 4 && getenv("IRK_NO_SHARED_UPPER") == nullptr) {
@@ -1542,6 +1726,7 @@ static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F
                 P.d_up0_rows + P.up0_ptr[l], n, b, c->T, P.d_rp, P.d_ci, P.d_voff, vals, dinv, y, z);
             c->launches++;
         }
+        tmark_end(c, tm, 7);
         return cuda_status(cudaGetLastError());
     }
     const int nup = (int)P.up_ptr.size() - 1;
@@ -1552,6 +1737,7 @@ static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F
             P.d_up_rows + P.up_ptr[l], n, b, P.d_rp, P.d_ci, P.d_voff, vals, dinv, y, z);
         c->launches++;
     }
+    tmark_end(c, tm, 7);
     return cuda_status(cudaGetLastError());
 }
 

@@ -357,6 +357,88 @@ int launch_givens(irk_ctx *c, int j, int restart) {
     return cuda_status(cudaGetLastError());
 }
 
+// The same Arnoldi step with w kept in shared memory: CTA b owns the
+// contiguous slice [b*chunk, (b+1)*chunk) of w for the whole step, so each
+// Gram-Schmidt step streams only v_{i-1} (just read, mostly from L2) and v_i
+// and never rewrites w in HBM until the normalised result.  One CTA per SM;
+// used when a slice fits in shared memory.  Element operations as in
+// k_arnoldi (the partition of the reductions differs).
+template <class AR>
+__global__ void __launch_bounds__(1024) k_arnoldi_smem(long long N, long long chunk, int j, int R, vec8 *w,
+                                                       const vec8 *V, Scal *slots, double *H, double *cs,
+                                                       double *sn, double *g, double *est, vec8 *part,
+                                                       unsigned *bar, int *err) {
+    typedef typename AR::val val;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    vec8 *ws = reinterpret_cast<vec8 *>(smem_raw);
+    __shared__ val sh[32];
+    __shared__ int s_ok;
+    __shared__ double s_h;
+    const long long c0 = (long long)blockIdx.x * chunk;
+    const long long c1 = c0 + chunk < N ? c0 + chunk : N;
+    const int len = c1 > c0 ? (int)(c1 - c0) : 0;
+    for (int e = threadIdx.x; e < len; e += blockDim.x) ws[e] = w[c0 + e];
+    __syncthreads();
+    double hprev = 0.0;
+    for (int i = 0; i <= j + 1; ++i) {
+        const bool last = i == j + 1;
+        const vec8 *vp = i > 0 ? V + (long long)(i - 1) * N + c0 : nullptr;
+        const vec8 *vi = last ? nullptr : V + (long long)i * N + c0;
+        const float hh = (float)hprev;
+        const val nh = AR::neg(AR::coef(hprev, hh, (float)(hprev - (double)hh)));
+        typename AR::acc acc = AR::zero();
+        constexpr int U = 4;
+        for (int e = threadIdx.x; e < len; e += U * blockDim.x) {
+            val wv[U], pv[U], xv[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int ee = e + u * blockDim.x;
+                const bool ok = ee < len;
+                wv[u] = ok ? AR::ldv(ws + ee) : AR::from_float(0.f);
+                pv[u] = (ok && vp) ? AR::ld(vp + ee) : AR::from_float(0.f);
+                xv[u] = (ok && !last) ? AR::ld(vi + ee) : AR::from_float(0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int ee = e + u * blockDim.x;
+                if (ee >= len) break;
+                if (vp) {
+                    wv[u] = AR::add(wv[u], AR::mul(nh, pv[u]));
+                    AR::st(ws + ee, wv[u]);
+                }
+                AR::fma(acc, wv[u], last ? wv[u] : xv[u]);
+            }
+        }
+        vec8 *pb = part + (i & 1) * gridDim.x;
+        const val r = block_reduce<AR>(AR::value(acc), sh);
+        if (threadIdx.x == 0) AR::st(pb + blockIdx.x, r);
+        if (!grid_sync(bar, err, &s_ok)) return;
+        typename AR::acc a2 = AR::zero();
+        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) AR::add_to(a2, AR::ldcg(pb + q));
+        const val tot = block_reduce<AR>(AR::value(a2), sh);
+        if (threadIdx.x == 0) {
+            double d = AR::to_double(tot);
+            if (!isfinite(d)) {
+                if (blockIdx.x == 0) atomicOr(err, IRK_DEV_ERR_NONFINITE);
+                d = 0.0;
+            }
+            if (last) d = d > 0.0 ? sqrt(d) : 0.0;
+            s_h = d;
+            if (blockIdx.x == 0) {
+                scal_store_d(slots + 2 + i, d);
+                H[i * R + j] = d;
+            }
+        }
+        __syncthreads();
+        hprev = s_h;
+    }
+    const double inv = hprev != 0.0 ? 1.0 / hprev : 0.0;
+    const float ih = (float)inv;
+    const val iv = AR::coef(inv, ih, (float)(inv - (double)ih));
+    for (int e = threadIdx.x; e < len; e += blockDim.x) AR::st(w + c0 + e, AR::mul(AR::ldv(ws + e), iv));
+    if (blockIdx.x == 0 && threadIdx.x == 0) givens_col(j, R, H, cs, sn, g, est, err);
+}
+
 // Launch shape of k_arnoldi: every CTA resident (cooperative launch).  Few
 // large CTAs keep the grid barrier (one atomic per CTA on one counter) and
 // the all-CTA reduction (every CTA reads every partial) short: one
@@ -396,7 +478,45 @@ static ArnoldiShape arnoldi_shape(irk_ctx *c) {
 // The whole Arnoldi step j (orthogonalisation, normalisation, Givens) in one
 // launch; returns IRK_ERR_INVALID when the device cannot launch it (the
 // caller then issues the step as separate launches).
+// k_arnoldi_smem's launch, or false when its slices do not fit (or no
+// cooperative launch): one 1024-thread CTA per SM, chunk = ceil(N / SMs).
+static bool launch_arnoldi_smem(irk_ctx *c, int j, int restart, vec8 *w, int *rc) {
+    if (getenv("IRK_ARNOLDI_GLOBAL")) return false;
+    static std::mutex mu;
+    static int sms = -1, optin = 0, coop = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (sms < 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        }
+    }
+    if (!coop || sms <= 0 || sms * 2 > IRK_PART_SLOTS) return false;
+    long long N = c->N;
+    long long chunk = (N + sms - 1) / sms;
+    chunk = (chunk + 1) / 2 * 2;  // even: 16-byte aligned slices
+    const size_t smem = (size_t)chunk * sizeof(vec8);
+    if (smem + 4096 > (size_t)optin) return false;
+    const void *fn = c->df ? (const void *)k_arnoldi_smem<ArDF> : (const void *)k_arnoldi_smem<ArF64>;
+    if (irk_allow_max_smem(fn)) return false;
+    int jj = j, R = restart;
+    const vec8 *V = c->d_V;
+    Scal *slots = scal(c, 0);
+    double *est = &scal(c, 1)->d;
+    vec8 *part = reinterpret_cast<vec8 *>(c->d_part);
+    void *args[] = {&N, &chunk, &jj, &R, &w, &V, &slots, &c->d_H, &c->d_cs, &c->d_sn, &c->d_g, &est, &part,
+                    &c->d_gbar, &c->d_err};
+    *rc = cuda_status(cudaLaunchCooperativeKernel(fn, sms, 1024, args, smem, c->stream));
+    c->launches++;
+    return true;
+}
+
 int launch_arnoldi(irk_ctx *c, int j, int restart, vec8 *w) {
+    int rc = IRK_OK;
+    if (launch_arnoldi_smem(c, j, restart, w, &rc)) return rc;
     const ArnoldiShape sh = arnoldi_shape(c);
     if (sh.grid <= 0) return IRK_ERR_INVALID;
     long long N = c->N;

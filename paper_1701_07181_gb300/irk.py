@@ -50,7 +50,9 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_longlong), ("matvec_ms", ctypes.c_double),
                 ("precond_ms", ctypes.c_double), ("ortho_ms", ctypes.c_double),
                 ("n_matvec", ctypes.c_int), ("n_precond", ctypes.c_int), ("n_ortho", ctypes.c_int),
-                ("matvec_variant", ctypes.c_int)]
+                ("matvec_variant", ctypes.c_int), ("factor_assemble_ms", ctypes.c_double),
+                ("factor_products_ms", ctypes.c_double), ("factor_inverse_ms", ctypes.c_double),
+                ("sweep_fwd_ms", ctypes.c_double), ("sweep_bwd_ms", ctypes.c_double)]
 
 
 EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor", "irk_solve",
