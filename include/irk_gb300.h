@@ -345,9 +345,17 @@ typedef struct {
      * width 8/4/2 columns, 256/128 threads), 4-6 bulk-copy pipelined kernel
      * (2 or 3 shared-memory stages, one or two CTAs per SM; where a stage does
      * not fit or m is odd it runs variant 0's launch); -1 before the first
-     * product.  The environment variable IRK_MATVEC_VARIANT=<0..6>, read when a
-     * context makes its first product, pins the variant.  Every variant gives the same result bit for bit. */
+     * product.  The environment variable IRK_MATVEC_VARIANT=<0..6>, read when
+     * a context makes its first product, pins the variant.  Every variant
+     * gives the same result bit for bit. */
     int matvec_variant;
+    /* with irk_options.timing = 1: device time of the kernels of the last
+     * factorisation (assembly of the blocks, block products, inversion of
+     * the diagonal blocks) and of the forward and backward sweeps of the
+     * last irk_solve's preconditioner applications (per-level sweeps only;
+     * 0 for the persistent form) */
+    double factor_assemble_ms, factor_products_ms, factor_inverse_ms;
+    double sweep_fwd_ms, sweep_bwd_ms;
 } irk_stats;
 IRK_API int irk_get_stats(const irk_ctx *ctx, irk_stats *out);
 
