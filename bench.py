@@ -232,6 +232,41 @@ def run_reference(args):
     return 0
 
 
+def precision_variants(configs, dev, dt=0.1):
+    """Per workload and factor precision (binary64 / binary32 / bfloat16
+    storage, double-float Krylov; binary64 Krylov for binary64 factors):
+    iterations, time of one factorisation + solve, and the relative
+    difference of W from the binary64 path's W (which the tests pin to the
+    oracle)."""
+    import torch
+    from paper_1701_07181_gb300 import inputs, irk
+    out = {}
+    for name in configs:
+        P = inputs.config(name, seed=0)
+        t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+        rp, ci, J, M, R = t(P.row_ptr), t(P.col_idx), t(P.J), t(P.M), t(P.R)
+        res, ref = {}, None
+        for fprec in ("fp64", "fp32", "bf16"):
+            kry = "fp64" if fprec == "fp64" else "df64"
+            with irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec=fprec, krylov=kry,
+                            ordering="multicolor") as S:
+                S.solve(R, 2 * dt, rtol=RTOL)  # warm-up (and autotuning)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                W, it, rr, rc = S.solve(R, dt, rtol=RTOL)
+                e1.record()
+                torch.cuda.synchronize()
+            Wn = W.cpu().numpy()
+            if ref is None:
+                ref = Wn
+            res[fprec + "_factors"] = {"krylov": kry, "iters": it, "relres": rr, "ms": e0.elapsed_time(e1),
+                                       "rel_diff_from_fp64": float(np.linalg.norm(Wn - ref) / np.linalg.norm(ref))}
+        out[name] = {"T": P.T, "m": P.m, "s": P.s, "dt": dt, **res}
+        del rp, ci, J, M, R
+    return out
+
+
 def dirk_comparison(P, dev, rp, ci, J, M, dt=0.1, reps=3):
     """Equal-order IRK vs DIRK steps of M u' = J u on the benchmark mesh
     (Sec. 5's comparison): RADAU23 vs DIRK33 and RADAU35 vs ESDIRK65.  One
@@ -352,6 +387,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-dirk", action="store_true")
+    ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--uneven-requests", type=int, default=128)
     ap.add_argument("--serving-requests", type=int, default=60)
     args = ap.parse_args()
@@ -494,6 +530,8 @@ def main():
             "last_solve": {"iters": st_last["iters"], "relres": st_last["relres"]}}
     if not args.no_dirk and world == 1:
         line["dirk_comparison"] = dirk_comparison(P, dev, rp, ci, J, M)
+    if not args.no_variants and world == 1:
+        line["precision_variants"] = precision_variants(("c1", "c2"), dev)
     if not args.no_serving and world == 1 and args.uneven_requests > 0:
         # batched uneven: independent 2D meshes of 500-5000 triangles, p 1..3,
         # s 2..3, all submitted at once (continuous batching of a backlog)
