@@ -145,16 +145,19 @@ int read_host(void *dst, const void *src, size_t bytes, int mem_space) {
 // Wait for the context's stream and read the device error word (an ordered
 // copy on the same stream into pinned memory: no device-wide synchronisation,
 // so contexts on different streams do not serialise each other).
+int err_code(int err) {
+    if (err & IRK_DEV_ERR_SINGULAR) return IRK_ERR_SINGULAR;
+    if (err & IRK_DEV_ERR_NONFINITE) return IRK_ERR_NONFINITE;
+    if (err & IRK_DEV_ERR_TIMEOUT) return IRK_ERR_TIMEOUT;
+    return IRK_OK;
+}
+
 int sync_err(irk_ctx *c) {
     int *herr = reinterpret_cast<int *>(c->h_scal + 3);
     cudaError_t e = cudaMemcpyAsync(herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) return cuda_status(e);
-    const int err = *herr;
-    if (err & IRK_DEV_ERR_SINGULAR) return IRK_ERR_SINGULAR;
-    if (err & IRK_DEV_ERR_NONFINITE) return IRK_ERR_NONFINITE;
-    if (err & IRK_DEV_ERR_TIMEOUT) return IRK_ERR_TIMEOUT;
-    return IRK_OK;
+    return err_code(*herr);
 }
 
 // Load J and M (row-major binary64 in mem_space) into the context's
@@ -568,6 +571,7 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
             tmark_end(c, tm, 0);
             tm = tmark_begin(c);
             rc = launch_arnoldi(c, j, Rs, w);
+            const bool one_launch = rc != IRK_ERR_INVALID;
             if (rc == IRK_ERR_INVALID) {
                 // no cooperative launch: one launch per Gram-Schmidt step
                 rc = IRK_OK;
@@ -585,11 +589,22 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
             ++total;
             jl = j;
             // residual estimate and h_{j+1,j} (kept in its scalar slot: the
-            // rotation zeroes H[j+1][j]) for the stopping and breakdown tests
-            cudaMemcpyAsync(est_h, irk_est_ptr(c), sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-            cudaMemcpyAsync(hn_h, reinterpret_cast<char *>(c->d_scal) + (size_t)(2 + j + 1) * IRK_SCAL_BYTES,
-                            sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-            if ((rc = sync_err(c))) break;
+            // rotation zeroes H[j+1][j]) for the stopping and breakdown tests;
+            // the one-launch step leaves them with the error word in one block
+            if (one_launch) {
+                double *st = c->h_scal + 8;
+                if ((rc = cuda_status(cudaMemcpyAsync(st, irk_status_ptr(c), 3 * sizeof(double),
+                                                      cudaMemcpyDeviceToHost, c->stream))) ||
+                    (rc = cuda_status(cudaStreamSynchronize(c->stream))) || (rc = err_code((int)st[2])))
+                    break;
+                *est_h = st[0];
+                *hn_h = st[1];
+            } else {
+                cudaMemcpyAsync(est_h, irk_est_ptr(c), sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+                cudaMemcpyAsync(hn_h, reinterpret_cast<char *>(c->d_scal) + (size_t)(2 + j + 1) * IRK_SCAL_BYTES,
+                                sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+                if ((rc = sync_err(c))) break;
+            }
             if (*est_h <= rtol * bnorm || total >= c->opt.max_iter || *hn_h == 0.0) break;
         }
         if (rc) break;

@@ -143,7 +143,11 @@ int launch_scale_slot(irk_ctx *c, vec8 *w, int slot);
 // Givens step for column j; writes the residual estimate to slot 1
 int launch_givens(irk_ctx *c, int j, int restart);
 // back-substitution for y (size jl+1) and x += Z y
+// returns IRK_ERR_INVALID when no cooperative launch is possible (the caller
+// runs the step as separate launches); on success the kernel has written
+// the iteration's status block (irk_status_ptr: estimate, h_{j+1,j}, error word)
 int launch_arnoldi(irk_ctx *c, int j, int restart, vec8 *w);
+double *irk_status_ptr(irk_ctx *c);
 int launch_lsq_update(irk_ctx *c, int jl, int restart);
 // g = (beta, 0, ..., 0) with beta from slot 0
 int launch_cycle_start(irk_ctx *c, int restart);

@@ -150,6 +150,16 @@ __global__ void k_givens(int j, int R, double *H, double *cs, double *sn, double
     givens_col(j, R, H, cs, sn, g, est, err);
 }
 
+// The iteration's status for the host in one 24-byte block: residual
+// estimate, h_{j+1,j} and the device error word (as a double), written by
+// CTA 0 last (also when it leaves on a barrier timeout), so one copy replaces
+// three.
+__device__ __forceinline__ void arnoldi_status(double *status, double est, double hn, int *err) {
+    status[0] = est;
+    status[1] = hn;
+    status[2] = (double)*reinterpret_cast<volatile int *>(err);
+}
+
 // Bounded grid-wide barrier of a cooperative launch (every CTA resident):
 // bar[0] counts the arrivals of the current generation, bar[1] is the
 // generation.  After IRK_SPIN_LIMIT polls a CTA records a timeout and the
@@ -199,7 +209,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, int *err, int *s_ok) {
 template <class AR, int NT>
 __global__ void __launch_bounds__(NT) k_arnoldi(long long N, int j, int R, vec8 *w, const vec8 *V, Scal *slots,
                                                  double *H, double *cs, double *sn, double *g, double *est,
-                                                 vec8 *part, unsigned *bar, int *err) {
+                                                 vec8 *part, unsigned *bar, int *err, double *status) {
     typedef typename AR::val val;
     __shared__ val sh[32];
     __shared__ int s_ok;
@@ -241,7 +251,10 @@ __global__ void __launch_bounds__(NT) k_arnoldi(long long N, int j, int R, vec8 
         vec8 *pb = part + (i & 1) * gridDim.x;
         const val r = block_reduce<AR>(AR::value(acc), sh);
         if (threadIdx.x == 0) AR::st(pb + blockIdx.x, r);
-        if (!grid_sync(bar, err, &s_ok)) return;
+        if (!grid_sync(bar, err, &s_ok)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) arnoldi_status(status, 0.0, 0.0, err);
+            return;
+        }
         typename AR::acc a2 = AR::zero();
         for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) AR::add_to(a2, AR::ldcg(pb + q));
         const val tot = block_reduce<AR>(AR::value(a2), sh);
@@ -271,7 +284,10 @@ __global__ void __launch_bounds__(NT) k_arnoldi(long long N, int j, int R, vec8 
         AR::st(w + e, AR::mul(a0, iv));
         if (e2 < N) AR::st(w + e2, AR::mul(a1, iv));
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) givens_col(j, R, H, cs, sn, g, est, err);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        givens_col(j, R, H, cs, sn, g, est, err);
+        arnoldi_status(status, *est, hprev, err);
+    }
 }
 
 // y = H(0:jl, 0:jl)^{-1} g(0:jl) (one thread), stored as Scal for the update.
@@ -324,6 +340,8 @@ int grid_stream(long long n) {
 static Scal *scal(irk_ctx *c, int slot) { return reinterpret_cast<Scal *>(c->d_scal) + slot; }
 
 double *irk_est_ptr(irk_ctx *c) { return &scal(c, 1)->d; }
+// status block of k_arnoldi (last scalar slot: 4 doubles)
+double *irk_status_ptr(irk_ctx *c) { return &scal(c, IRK_SCAL_SLOTS - 1)->d; }
 double *irk_beta_ptr(irk_ctx *c) { return &scal(c, 0)->d; }
 
 int launch_axpy_dot_slot(irk_ctx *c, vec8 *w, const vec8 *vprev, int hprev_slot, const vec8 *v,
@@ -367,7 +385,7 @@ template <class AR>
 __global__ void __launch_bounds__(1024) k_arnoldi_smem(long long N, long long chunk, int j, int R, vec8 *w,
                                                        const vec8 *V, Scal *slots, double *H, double *cs,
                                                        double *sn, double *g, double *est, vec8 *part,
-                                                       unsigned *bar, int *err) {
+                                                       unsigned *bar, int *err, double *status) {
     typedef typename AR::val val;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec8 *ws = reinterpret_cast<vec8 *>(smem_raw);
@@ -412,7 +430,10 @@ __global__ void __launch_bounds__(1024) k_arnoldi_smem(long long N, long long ch
         vec8 *pb = part + (i & 1) * gridDim.x;
         const val r = block_reduce<AR>(AR::value(acc), sh);
         if (threadIdx.x == 0) AR::st(pb + blockIdx.x, r);
-        if (!grid_sync(bar, err, &s_ok)) return;
+        if (!grid_sync(bar, err, &s_ok)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) arnoldi_status(status, 0.0, 0.0, err);
+            return;
+        }
         typename AR::acc a2 = AR::zero();
         for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) AR::add_to(a2, AR::ldcg(pb + q));
         const val tot = block_reduce<AR>(AR::value(a2), sh);
@@ -436,7 +457,10 @@ __global__ void __launch_bounds__(1024) k_arnoldi_smem(long long N, long long ch
     const float ih = (float)inv;
     const val iv = AR::coef(inv, ih, (float)(inv - (double)ih));
     for (int e = threadIdx.x; e < len; e += blockDim.x) AR::st(w + c0 + e, AR::mul(AR::ldv(ws + e), iv));
-    if (blockIdx.x == 0 && threadIdx.x == 0) givens_col(j, R, H, cs, sn, g, est, err);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        givens_col(j, R, H, cs, sn, g, est, err);
+        arnoldi_status(status, *est, hprev, err);
+    }
 }
 
 // Launch shape of k_arnoldi: every CTA resident (cooperative launch).  Few
@@ -507,8 +531,9 @@ static bool launch_arnoldi_smem(irk_ctx *c, int j, int restart, vec8 *w, int *rc
     Scal *slots = scal(c, 0);
     double *est = &scal(c, 1)->d;
     vec8 *part = reinterpret_cast<vec8 *>(c->d_part);
+    double *status = irk_status_ptr(c);
     void *args[] = {&N, &chunk, &jj, &R, &w, &V, &slots, &c->d_H, &c->d_cs, &c->d_sn, &c->d_g, &est, &part,
-                    &c->d_gbar, &c->d_err};
+                    &c->d_gbar, &c->d_err, &status};
     *rc = cuda_status(cudaLaunchCooperativeKernel(fn, sms, 1024, args, smem, c->stream));
     c->launches++;
     return true;
@@ -525,8 +550,9 @@ int launch_arnoldi(irk_ctx *c, int j, int restart, vec8 *w) {
     Scal *slots = scal(c, 0);
     double *est = &scal(c, 1)->d;
     vec8 *part = reinterpret_cast<vec8 *>(c->d_part);
+    double *status = irk_status_ptr(c);
     void *args[] = {&N, &jj, &R, &w, &V, &slots, &c->d_H, &c->d_cs, &c->d_sn, &c->d_g, &est, &part, &c->d_gbar,
-                    &c->d_err};
+                    &c->d_err, &status};
     const void *fn;
     if (c->df)
         fn = sh.threads == 256 ? (const void *)k_arnoldi<ArDF, 256> : (const void *)k_arnoldi<ArDF, 1024>;
