@@ -323,7 +323,7 @@ def dirk_comparison(P, dev, rp, ci, J, M, dt=0.1, reps=3):
     return out
 
 
-def kernel_rooflines(P, r, acc, hbm_peak, peak_kind):
+def kernel_rooflines(P, r, acc, hbm_peak, peak_kind, two_colour=False):
     """Per-kernel measured time (CUDA events, irk_options.timing) over the
     timed solves, algorithmic bytes or flops per unit, and the roofline of
     the kernel with the largest total time."""
@@ -336,11 +336,23 @@ def kernel_rooflines(P, r, acc, hbm_peak, peak_kind):
     tf32_peak = MEASURED_BF16 * 1.1 / 2.25 if MEASURED_BF16 else 1100.0  # nominal tf32 / bf16 ratio
     napp = max(1, acc["n_precond"])
     nfac = max(1, len(acc["iters"]))
+    if two_colour:
+        # first launch: forward rows of the second colour (nb elements, each
+        # with its r neighbours below it) and their D^-1 products; second
+        # launch: backward rows of the first colour, upper blocks once for
+        # all stages; binary32 blocks, double-float v and z, binary32 y
+        nb = lower // r
+        na = T - nb
+        fwd = 4 * s * lower * mm + 4 * s * nb * mm + 8 * s * n + 12 * s * nb * m
+        bwd = 4 * lower * mm + 4 * s * na * mm + 8 * s * na * m + 4 * s * nb * m + 12 * s * na * m
+    else:
+        fwd = 4 * s * lower * mm + 8 * s * n + 4 * s * n
+        bwd = 4 * lower * mm + 4 * s * mm * T + 16 * s * n
     rows = {
         # name: (total ms, units, algorithmic amount per unit, kind)
         "matvec": (acc["matvec_ms"], acc["n_matvec"], 8 * (r + 1) * mm * T + 8 * mm * T + 16 * s * n, "hbm"),
-        "sweep_fwd": (acc.get("sweep_fwd_ms", 0.0), napp, 4 * s * lower * mm + 8 * s * n + 4 * s * n, "hbm"),
-        "sweep_bwd": (acc.get("sweep_bwd_ms", 0.0), napp, 4 * lower * mm + 4 * s * mm * T + 16 * s * n, "hbm"),
+        "sweep_fwd": (acc.get("sweep_fwd_ms", 0.0), napp, fwd, "hbm"),
+        "sweep_bwd": (acc.get("sweep_bwd_ms", 0.0), napp, bwd, "hbm"),
         "factor_assemble": (acc.get("factor_assemble_ms", 0.0), nfac,
                             8 * nnzb * mm + 8 * mm * T + 4 * s * nnzb * mm, "hbm"),
         "factor_products": (acc.get("factor_products_ms", 0.0), nfac, 4.0 * s * lower * m ** 3, "tensor"),
@@ -427,6 +439,7 @@ def main():
                     acc[k] = acc.get(k, 0.0) + st[k]
                 for k in ("n_matvec", "n_precond", "n_ortho"):
                     acc[k] += st[k]
+                acc["two_colour"] = acc.get("two_colour", True) and st["sweep_two_colour"] == 1
 
     def barrier():
         if dist is not None:
@@ -512,7 +525,9 @@ def main():
         return 0
 
     peak, peak_kind = peaks()
-    roofline, kernels = kernel_rooflines(P, r, acc, peak, peak_kind)
+    roofline, kernels = kernel_rooflines(P, r, acc, peak, peak_kind, two_colour=acc.get("two_colour", False))
+    kernels["sweep_form"] = ("two-colour: forward rows of the second colour with their D^-1 products, then the "
+                             "first colour's backward rows" if acc.get("two_colour") else "level sweeps")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "df64 Krylov / f32 factors",

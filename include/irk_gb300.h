@@ -344,8 +344,10 @@ typedef struct {
      * context's (m, s, arithmetic): 0-3 register-streaming kernel (chunk
      * width 8/4/2 columns, 256/128 threads), 4-6 bulk-copy pipelined kernel
      * (2 or 3 shared-memory stages, one or two CTAs per SM; where a stage does
-     * not fit or m is odd it runs variant 0's launch); -1 before the first
-     * product.  The environment variable IRK_MATVEC_VARIANT=<0..6>, read when
+     * not fit or m is odd it runs variant 0's launch), 7 register-streaming
+     * kernel with the block size fixed at compile time (double-float Krylov,
+     * s = 2..4, m = 12, 20, 24, 40 or 50; else variant 0's launch); -1 before
+     * the first product.  The environment variable IRK_MATVEC_VARIANT=<0..7>, read when
      * a context makes its first product, pins the variant.  Every variant
      * gives the same result bit for bit. */
     int matvec_variant;
@@ -356,6 +358,18 @@ typedef struct {
      * 0 for the persistent form) */
     double factor_assemble_ms, factor_products_ms, factor_inverse_ms;
     double sweep_fwd_ms, sweep_bwd_ms;
+    /* levels of the last factorisation whose block products ran as whole
+     * staged rows (binary32 factors, every update of a lower block landing on
+     * its row's diagonal block: Alg. 2 with the row's products independent);
+     * the environment variable IRK_NO_FUSED_FACTOR turns that kernel off */
+    int factor_fused_levels;
+    /* 1 when the last preconditioner application ran in the two-colour form:
+     * two launches, the forward sweep of the second colour fused with its
+     * diagonal-block products, then the backward sweep of the first colour
+     * (two lower levels, the second without upper entries, as the
+     * two-colour order gives on a two-colourable mesh); 0 otherwise.  The
+     * environment variable IRK_NO_TWO_COLOUR turns that form off. */
+    int sweep_two_colour;
 } irk_stats;
 IRK_API int irk_get_stats(const irk_ctx *ctx, irk_stats *out);
 

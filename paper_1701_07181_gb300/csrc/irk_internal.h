@@ -51,6 +51,13 @@ struct PcSystem {
     int shared_upper = 0;
     std::vector<int> up0_ptr;
     int *d_up0_rows = nullptr;
+    // every factor update of a lower entry lands on its row's diagonal block:
+    // most lower entries of a row (the fused factorisation kernel), else 0
+    int fused_r = 0;
+    // two lower levels, the second without upper entries, the first level of
+    // the upper DAG without lower entries, together every row: the
+    // preconditioner applies in two launches (k_sweep_fd, k_sweep_bu)
+    int two_colour = 0;
     // values, column-major blocks: working precision (double or float)
     void *d_vals = nullptr, *d_dinv = nullptr;
     // bf16 copies used by the sweeps when factor_prec == IRK_FACTOR_BF16

@@ -21,6 +21,7 @@
 #include <algorithm>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "arith.cuh"
@@ -66,10 +67,7 @@ int gj_threads() {
     static const int t = std::max(32, std::min(256, env_int("IRK_GJ_THREADS", 128)));
     return t;
 }
-int gj_split_min() {
-    static const int n = env_int("IRK_GJ_SPLIT_MIN", 2048);
-    return n;
-}
+int gj_split_min() { return env_int("IRK_GJ_SPLIT_MIN", 2048); }
 
 // ---------------------------------------------------------------------------
 // factor-storage loads (binary64, binary32 or bfloat16 storage)
@@ -142,6 +140,13 @@ __global__ void __launch_bounds__(256) k_assemble(long long nnz, int m, const As
 // M blocks), so one CTA reads a J block (and the mass block on the
 // diagonal) once and writes all s assembled blocks d_k M - dt J, each with
 // k_assemble's arithmetic.  Entries are read from stage 0's part of the table.
+__device__ __forceinline__ void store_pair(float *p, const float (&v)[2]) {
+    *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+}
+__device__ __forceinline__ void store_pair(double *p, const double (&v)[2]) {
+    *reinterpret_cast<double2 *>(p) = make_double2(v[0], v[1]);
+}
+
 template <class C>
 __global__ void __launch_bounds__(256) k_assemble_stages(long long per_stage, int s, int m, const AsmEntry *ent,
                                                          const vec8 *J, const vec8 *M, int df, AsmTables tab,
@@ -155,6 +160,48 @@ __global__ void __launch_bounds__(256) k_assemble_stages(long long per_stage, in
         C cmk[IRK_MAX_S];
 #pragma unroll
         for (int k = 0; k < IRK_MAX_S; ++k) cmk[k] = (Mb && k < s) ? (C)tab.cm[k * s + k] : C(0);
+        if ((mm & 1) == 0) {
+            // pairs of entries: 16-byte loads of J and M, two pairs per
+            // thread with every load issued before the stores
+            const int pairs = mm >> 1;
+            const uint4 *J2 = reinterpret_cast<const uint4 *>(Jb), *M2 = reinterpret_cast<const uint4 *>(Mb);
+            for (int e0 = threadIdx.x; e0 < pairs; e0 += 2 * blockDim.x) {
+                uint4 jr[2], mr[2];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    const bool ok = e < pairs;
+                    jr[u] = (ok && Jb) ? __ldg(J2 + e) : make_uint4(0, 0, 0, 0);
+                    mr[u] = (ok && Mb) ? __ldg(M2 + e) : make_uint4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const int e = e0 + u * blockDim.x;
+                    if (e >= pairs) break;
+                    C mv[2], jv[2];
+                    const vec8 jraw[2] = {((vec8)jr[u].y << 32) | jr[u].x, ((vec8)jr[u].w << 32) | jr[u].z};
+                    const vec8 mraw[2] = {((vec8)mr[u].y << 32) | mr[u].x, ((vec8)mr[u].w << 32) | mr[u].z};
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        mv[h] = Mb ? CT<C>::from_store(mraw[h], df) : C(0);
+                        jv[h] = Jb ? CT<C>::from_store(jraw[h], df) : C(0);
+                    }
+#pragma unroll
+                    for (int k = 0; k < IRK_MAX_S; ++k) {
+                        if (k >= s) break;
+                        C v[2];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            v[h] = C(0);
+                            if (Mb) v[h] += cmk[k] * mv[h];
+                            if (Jb) v[h] += cj * jv[h];
+                        }
+                        store_pair(vals + (q + k * per_stage) * mm + 2 * e, v);
+                    }
+                }
+            }
+            continue;
+        }
         for (int r = threadIdx.x; r < mm; r += blockDim.x) {
             const C mv = Mb ? CT<C>::from_store(Mb[r], df) : C(0);
             const C jv = Jb ? CT<C>::from_store(Jb[r], df) : C(0);
@@ -519,52 +566,71 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-__device__ void tc_gemm(float *dst1, float *dst2, const float *X, const float *Y, int b, int mode) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+// One 16 x 8 output tile of X * Y (column-major b x b operands in shared
+// memory) accumulated into d with 3xTF32: each operand split into a TF32 high
+// part and a TF32 remainder, three m16n8k8 products per k-step (the small
+// terms first).
+__device__ __forceinline__ void tc_tile(float (&d)[4], const float *X, const float *Y, int b, int r0, int c0) {
+    const int lane = threadIdx.x & 31;
     const int g = lane >> 2, t = lane & 3;
-    const int mt = (b + 15) / 16, nt = (b + 7) / 8, kt = (b + 7) / 8;
+    const int kt = (b + 7) / 8;
+    for (int kk = 0; kk < kt; ++kk) {
+        const int k0 = kk * 8;
+        float av[4], bv[2];
+        const int ar[4] = {r0 + g, r0 + g + 8, r0 + g, r0 + g + 8};
+        const int ak[4] = {k0 + t, k0 + t, k0 + t + 4, k0 + t + 4};
+#pragma unroll
+        for (int q = 0; q < 4; ++q) av[q] = (ar[q] < b && ak[q] < b) ? X[ak[q] * b + ar[q]] : 0.f;
+        const int bk[2] = {k0 + t, k0 + t + 4};
+        const int bc = c0 + g;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) bv[q] = (bk[q] < b && bc < b) ? Y[bc * b + bk[q]] : 0.f;
+        unsigned ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ah[q] = to_tf32(av[q]);
+            al[q] = to_tf32(av[q] - __uint_as_float(ah[q]));
+        }
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            bh[q] = to_tf32(bv[q]);
+            bl[q] = to_tf32(bv[q] - __uint_as_float(bh[q]));
+        }
+        mma_tf32(d, al, bh);  // small terms first
+        mma_tf32(d, ah, bl);
+        mma_tf32(d, ah, bh);
+    }
+}
+
+// Writes (mode 0: dst1 = d, and dst2 = d when non-null) or subtracts
+// (mode 1: dst1 -= d) a tile's accumulator.
+__device__ __forceinline__ void tc_store(const float (&d)[4], float *dst1, float *dst2, int b, int r0, int c0,
+                                         int mode) {
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int rr[4] = {r0 + g, r0 + g, r0 + g + 8, r0 + g + 8};
+    const int cc[4] = {c0 + 2 * t, c0 + 2 * t + 1, c0 + 2 * t, c0 + 2 * t + 1};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        if (rr[q] >= b || cc[q] >= b) continue;
+        const int e = cc[q] * b + rr[q];
+        if (mode == 0) {
+            dst1[e] = d[q];
+            if (dst2) dst2[e] = d[q];
+        } else {
+            dst1[e] -= d[q];
+        }
+    }
+}
+
+__device__ void tc_gemm(float *dst1, float *dst2, const float *X, const float *Y, int b, int mode) {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int mt = (b + 15) / 16, nt = (b + 7) / 8;
     for (int tile = warp; tile < mt * nt; tile += nwarps) {
         const int r0 = (tile % mt) * 16, c0 = (tile / mt) * 8;
         float d[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int kk = 0; kk < kt; ++kk) {
-            const int k0 = kk * 8;
-            float av[4], bv[2];
-            const int ar[4] = {r0 + g, r0 + g + 8, r0 + g, r0 + g + 8};
-            const int ak[4] = {k0 + t, k0 + t, k0 + t + 4, k0 + t + 4};
-#pragma unroll
-            for (int q = 0; q < 4; ++q) av[q] = (ar[q] < b && ak[q] < b) ? X[ak[q] * b + ar[q]] : 0.f;
-            const int bk[2] = {k0 + t, k0 + t + 4};
-            const int bc = c0 + g;
-#pragma unroll
-            for (int q = 0; q < 2; ++q) bv[q] = (bk[q] < b && bc < b) ? Y[bc * b + bk[q]] : 0.f;
-            unsigned ah[4], al[4], bh[2], bl[2];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                ah[q] = to_tf32(av[q]);
-                al[q] = to_tf32(av[q] - __uint_as_float(ah[q]));
-            }
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                bh[q] = to_tf32(bv[q]);
-                bl[q] = to_tf32(bv[q] - __uint_as_float(bh[q]));
-            }
-            mma_tf32(d, al, bh);  // small terms first
-            mma_tf32(d, ah, bl);
-            mma_tf32(d, ah, bh);
-        }
-        const int rr[4] = {r0 + g, r0 + g, r0 + g + 8, r0 + g + 8};
-        const int cc[4] = {c0 + 2 * t, c0 + 2 * t + 1, c0 + 2 * t, c0 + 2 * t + 1};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            if (rr[q] >= b || cc[q] >= b) continue;
-            const int e = cc[q] * b + rr[q];
-            if (mode == 0) {
-                dst1[e] = d[q];
-                if (dst2) dst2[e] = d[q];
-            } else {
-                dst1[e] -= d[q];
-            }
-        }
+        tc_tile(d, X, Y, b, r0, c0);
+        tc_store(d, dst1, dst2, b, r0, c0, mode);
     }
 }
 
@@ -647,6 +713,257 @@ __global__ void __launch_bounds__(256) k_factor_level2(const int *rows, int b, c
     const bool ok = gauss_jordan3(X, Y, b, fcol, b + 1);
     for (int e = threadIdx.x; e < bb; e += blockDim.x) dinv[(long long)R * bb + e] = Y[e];
     if (!ok && threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_SINGULAR);
+}
+
+// Factorisation of one level (binary32 factors) when every update of a row
+// lands on its own diagonal block: the lower neighbours i_1 < ... < i_r of a
+// row are pairwise non-adjacent, so the only update of entry p is
+// D -= L_p U_p with U_p the block (i_p, R).  The row's blocks are then
+// independent of one another's products:
+//   phase 1: L_p = B_p D_{i_p}^{-1} for all p at once, spread over the warps;
+//   phase 2: D -= [L_1 ... L_r] [U_1; ...; U_r], one 3xTF32 product of inner
+//            size r b accumulated per 16 x 8 tile of D.
+// One thread stages the row by bulk copies (B_p and D_i^{-1} on one
+// mbarrier, U_p and D on a second, waited for only before phase 2).  Phase-1
+// accumulators stay in registers (at most IRK_FUSED_TPW tiles per warp) until
+// every warp is past its reads of B_p, then overwrite B_p in shared memory.
+// The diagonal blocks are inverted afterwards by the inversion kernel.
+// Shared memory: 1 + 3 rmax block slots (128-byte aligned) + two barriers.
+#define IRK_FUSED_TPW 8
+
+__device__ __forceinline__ void copy_block_out(float *dst, const float *src, int bb) {
+    const float4 *s4 = reinterpret_cast<const float4 *>(src);
+    float4 *d4 = reinterpret_cast<float4 *>(dst);
+    for (int e = threadIdx.x; e < bb / 4; e += blockDim.x) d4[e] = s4[e];
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_factor_fused(const int *rows, int b, const int *rp, const int *ci,
+                                                          const int *diag, const int *upd_ptr, const int *upd,
+                                                          float *vals, const float *dinv, int rmax, int *err) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    const int bb = b * b;
+    const unsigned blk = (unsigned)bb * 4u;  // a multiple of 16 (b even)
+    const size_t stride = ((size_t)blk + 127) / 128 * 128;
+    auto slot = [&](int j) { return reinterpret_cast<float *>(smem_raw + stride * j); };
+    float *D = slot(0);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem_raw + stride * (1 + 3 * rmax));
+    const int R = rows[blockIdx.x];
+    const int p0 = rp[R], pend = rp[R + 1];
+    int r = 0;
+    while (r < rmax && p0 + r < pend && ci[p0 + r] < R) ++r;
+    const long long dpos = diag[R];
+    if (threadIdx.x == 0) {
+        mbar_init(bars);
+        mbar_init(bars + 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_arrive(bars, 2u * r * blk);
+        for (int p = 0; p < r; ++p) {
+            tma_load_1d(slot(1 + p), vals + (long long)(p0 + p) * bb, blk, bars);
+            tma_load_1d(slot(1 + rmax + p), dinv + (long long)ci[p0 + p] * bb, blk, bars);
+        }
+        mbar_expect_arrive(bars + 1, (unsigned)(r + 1) * blk);
+        tma_load_1d(D, vals + dpos * bb, blk, bars + 1);
+        for (int p = 0; p < r; ++p)
+            tma_load_1d(slot(1 + 2 * rmax + p), vals + (long long)upd[2 * upd_ptr[p0 + p] + 1] * bb, blk, bars + 1);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5;
+    const int mt = (b + 15) / 16, nt = (b + 7) / 8, ntile = mt * nt;
+    // a wait that gives up: every thread drains both barriers (bounded) and
+    // the CTA leaves together
+    const bool ok0 = mbar_wait(bars, 0);
+    if (__syncthreads_or(!ok0)) {
+        if (threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+        mbar_wait(bars, 0);
+        mbar_wait(bars + 1, 0);
+        return;
+    }
+    // phase 1: L_p tiles, item = p * ntile + tile
+    float acc[IRK_FUSED_TPW][4];
+#pragma unroll
+    for (int j = 0; j < IRK_FUSED_TPW; ++j) {
+        acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+        const int item = warp + j * NW;
+        if (item < r * ntile) {
+            const int p = item / ntile, t = item - p * ntile;
+            tc_tile(acc[j], slot(1 + p), slot(1 + rmax + p), b, (t % mt) * 16, (t / mt) * 8);
+        }
+    }
+    __syncthreads();  // every read of B_p done
+#pragma unroll
+    for (int j = 0; j < IRK_FUSED_TPW; ++j) {
+        const int item = warp + j * NW;
+        if (item < r * ntile) {
+            const int p = item / ntile, t = item - p * ntile;
+            tc_store(acc[j], slot(1 + p), nullptr, b, (t % mt) * 16, (t / mt) * 8, 0);
+        }
+    }
+    const bool ok1 = mbar_wait(bars + 1, 0);
+    if (__syncthreads_or(!ok1)) {  // also publishes the L_p tiles
+        if (threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+        mbar_wait(bars + 1, 0);
+        return;
+    }
+    for (int p = 0; p < r; ++p) copy_block_out(vals + (long long)(p0 + p) * bb, slot(1 + p), bb);
+    // phase 2: each warp owns tiles of D
+    for (int t = warp; t < ntile; t += NW) {
+        float d[4] = {0.f, 0.f, 0.f, 0.f};
+        const int r0 = (t % mt) * 16, c0 = (t / mt) * 8;
+        for (int p = 0; p < r; ++p) tc_tile(d, slot(1 + p), slot(1 + 2 * rmax + p), b, r0, c0);
+        tc_store(d, D, nullptr, b, r0, c0, 1);
+    }
+    __syncthreads();
+    copy_block_out(vals + dpos * bb, D, bb);
+}
+
+// The same staged-row factorisation with the block size known at compile
+// time.  Work is cut into row strips instead of tiles: a warp computes the
+// 16 x B strip X[r0:r0+16, :] Y of a product, so each A fragment is loaded
+// and split into TF32 high / remainder parts once per k-step and used for
+// all ceil(B/8) column tiles, and every index is a constant.
+//   phase 1: item (p, strip): L_p's strip, written over the same rows of B_p
+//            in shared memory (only this warp reads those rows);
+//   phase 2: item (strip, p): the partial P_p = L_p U_p of the strip, written
+//            into D_{i_p}^{-1}'s slot (free after phase 1);
+//   then D - ((P_1 + P_2) + ...) in a fixed order, straight to global memory.
+template <int B>
+__device__ __forceinline__ void strip_product(float (&acc)[(B + 7) / 8][4], const float *X, const float *Y, int r0) {
+    constexpr int NT = (B + 7) / 8, KT = (B + 7) / 8;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+    const int ra = r0 + g, rb = r0 + g + 8;
+    const bool oka = ra < B, okb = rb < B;
+#pragma unroll
+    for (int kk = 0; kk < KT; ++kk) {
+        const int ka = kk * 8 + t, kb = kk * 8 + t + 4;
+        const bool ka_in = ka < B, kb_in = kb < B;
+        float av[4];
+        av[0] = (oka && ka_in) ? X[ka * B + ra] : 0.f;
+        av[1] = (okb && ka_in) ? X[ka * B + rb] : 0.f;
+        av[2] = (oka && kb_in) ? X[kb * B + ra] : 0.f;
+        av[3] = (okb && kb_in) ? X[kb * B + rb] : 0.f;
+        unsigned ah[4], al[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            ah[q] = to_tf32(av[q]);
+            al[q] = to_tf32(av[q] - __uint_as_float(ah[q]));
+        }
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+            const int col = n * 8 + g;
+            const bool cin = col < B;
+            const float b0 = (cin && ka_in) ? Y[col * B + ka] : 0.f;
+            const float b1 = (cin && kb_in) ? Y[col * B + kb] : 0.f;
+            unsigned bh[2], bl[2];
+            bh[0] = to_tf32(b0);
+            bl[0] = to_tf32(b0 - __uint_as_float(bh[0]));
+            bh[1] = to_tf32(b1);
+            bl[1] = to_tf32(b1 - __uint_as_float(bh[1]));
+            mma_tf32(acc[n], al, bh);  // small terms first
+            mma_tf32(acc[n], ah, bl);
+            mma_tf32(acc[n], ah, bh);
+        }
+    }
+}
+
+template <int B>
+__device__ __forceinline__ void strip_store(const float (&acc)[(B + 7) / 8][4], float *dst, int r0) {
+    constexpr int NT = (B + 7) / 8;
+    const int lane = threadIdx.x & 31;
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int n = 0; n < NT; ++n) {
+        const int c = n * 8 + 2 * t;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int row = r0 + g + (q >> 1) * 8, col = c + (q & 1);
+            if (row < B && col < B) dst[col * B + row] = acc[n][q];
+        }
+    }
+}
+
+template <int B>
+__global__ void __launch_bounds__(512) k_factor_fused_b(const int *rows, const int *rp, const int *ci,
+                                                        const int *diag, const int *upd_ptr, const int *upd,
+                                                        float *vals, const float *dinv, int rmax, int *err) {
+    constexpr int BB = B * B, MT = (B + 15) / 16, NT = (B + 7) / 8;
+    constexpr unsigned BLK = BB * 4u;  // a multiple of 16 (B even)
+    constexpr size_t STRIDE = ((size_t)BLK + 127) / 128 * 128;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    auto slot = [&](int j) { return reinterpret_cast<float *>(smem_raw + STRIDE * j); };
+    float *D = slot(0);
+    unsigned long long *bars = reinterpret_cast<unsigned long long *>(smem_raw + STRIDE * (1 + 3 * rmax));
+    const int R = rows[blockIdx.x];
+    const int p0 = rp[R], pend = rp[R + 1];
+    int r = 0;
+    while (r < rmax && p0 + r < pend && ci[p0 + r] < R) ++r;
+    const long long dpos = diag[R];
+    if (threadIdx.x == 0) {
+        mbar_init(bars);
+        mbar_init(bars + 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_arrive(bars, 2u * r * BLK);
+        for (int p = 0; p < r; ++p) {
+            tma_load_1d(slot(1 + p), vals + (long long)(p0 + p) * BB, BLK, bars);
+            tma_load_1d(slot(1 + rmax + p), dinv + (long long)ci[p0 + p] * BB, BLK, bars);
+        }
+        mbar_expect_arrive(bars + 1, (unsigned)(r + 1) * BLK);
+        tma_load_1d(D, vals + dpos * BB, BLK, bars + 1);
+        for (int p = 0; p < r; ++p)
+            tma_load_1d(slot(1 + 2 * rmax + p), vals + (long long)upd[2 * upd_ptr[p0 + p] + 1] * BB, BLK, bars + 1);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const bool ok0 = mbar_wait(bars, 0);
+    if (__syncthreads_or(!ok0)) {
+        if (threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+        mbar_wait(bars, 0);
+        mbar_wait(bars + 1, 0);
+        return;
+    }
+    // phase 1: L_p = B_p D_{i_p}^{-1}, strip by strip, in place over B_p
+    for (int it = warp; it < r * MT; it += nwarps) {
+        const int p = it / MT, r0 = (it - p * MT) * 16;
+        float acc[NT][4];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+        strip_product<B>(acc, slot(1 + p), slot(1 + rmax + p), r0);
+        strip_store<B>(acc, slot(1 + p), r0);
+    }
+    const bool ok1 = mbar_wait(bars + 1, 0);
+    if (__syncthreads_or(!ok1)) {  // also: every L_p complete, every D^{-1} read
+        if (threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+        mbar_wait(bars + 1, 0);
+        return;
+    }
+    for (int p = 0; p < r; ++p) copy_block_out(vals + (long long)(p0 + p) * BB, slot(1 + p), BB);
+    // phase 2: partial Schur products P_p = L_p U_p into the D^{-1} slots
+    for (int it = warp; it < r * MT; it += nwarps) {
+        const int p = it % r, r0 = (it / r) * 16;
+        float acc[NT][4];
+#pragma unroll
+        for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+        strip_product<B>(acc, slot(1 + p), slot(1 + 2 * rmax + p), r0);
+        strip_store<B>(acc, slot(1 + rmax + p), r0);
+    }
+    __syncthreads();
+    // D - sum_p P_p (fixed order), four elements per thread and step
+    float4 *out = reinterpret_cast<float4 *>(vals + dpos * BB);
+    for (int e = threadIdx.x; e < BB / 4; e += blockDim.x) {
+        float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int p = 0; p < r; ++p) {
+            const float4 v = reinterpret_cast<const float4 *>(slot(1 + rmax + p))[e];
+            s.x += v.x;
+            s.y += v.y;
+            s.z += v.z;
+            s.w += v.w;
+        }
+        const float4 d = reinterpret_cast<const float4 *>(D)[e];
+        out[e] = make_float4(d.x - s.x, d.y - s.y, d.z - s.z, d.w - s.w);
+    }
 }
 
 // D_R^{-1} for a list of rows whose diagonal block is final (rows without
@@ -758,11 +1075,60 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
+// The warp's pivot key at a step: binary32 values take a 32-bit max of the
+// magnitude bits over the unused rows (one redux.sync) and a ballot for the
+// lowest such row; binary64 keys go through the 64-bit shuffle max.  Both
+// give the key gjr_key would: largest magnitude, lowest row on ties, 0 when
+// every row of the warp is used.
+template <class C>
+__device__ __forceinline__ unsigned long long warp_pivot_key(C v, bool used, int r);
+template <>
+__device__ __forceinline__ unsigned long long warp_pivot_key<float>(float v, bool used, int r) {
+    const unsigned bits = used ? 0u : (v == v ? __float_as_uint(fabsf(v)) : 0u);
+    const unsigned mx = __reduce_max_sync(0xffffffffu, bits);
+    const unsigned bal = __ballot_sync(0xffffffffu, !used && bits == mx);
+    if (!bal) return 0ull;
+    const int row = (r & ~31) + __ffs(bal) - 1;
+    return ((unsigned long long)mx << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)row);
+}
+template <>
+__device__ __forceinline__ unsigned long long warp_pivot_key<double>(double v, bool used, int r) {
+    return warp_max_u64(used ? 0ull : gjr_key<double>(v, r));
+}
+
+// 16-byte shared-memory moves of the pivot row (4 floats or 2 doubles).
+template <class C>
+struct Vec16;
+template <>
+struct Vec16<float> {
+    static constexpr int W = 4;
+    static __device__ __forceinline__ void ld(float (&d)[4], const float *p) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        d[0] = v.x, d[1] = v.y, d[2] = v.z, d[3] = v.w;
+    }
+    static __device__ __forceinline__ void st(float *p, const float (&d)[4]) {
+        *reinterpret_cast<float4 *>(p) = make_float4(d[0], d[1], d[2], d[3]);
+    }
+};
+template <>
+struct Vec16<double> {
+    static constexpr int W = 2;
+    static __device__ __forceinline__ void ld(double (&d)[2], const double *p) {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        d[0] = v.x, d[1] = v.y;
+    }
+    static __device__ __forceinline__ void st(double *p, const double (&d)[2]) {
+        *reinterpret_cast<double2 *>(p) = make_double2(d[0], d[1]);
+    }
+};
+
 template <class C, int B>
 __global__ void __launch_bounds__((B + 31) / 32 * 32) k_factor_diag_rows(const int *rows, const int *diag,
                                                                           const C *vals, C *dinv, int *err) {
     constexpr int NW = (B + 31) / 32;
-    __shared__ C s_prow[2][B];
+    constexpr int VW = Vec16<C>::W;
+    constexpr int BP = (B + VW - 1) / VW * VW;  // pivot row padded to whole 16-byte moves
+    __shared__ __align__(16) C s_prow[2][BP];
     __shared__ unsigned long long s_key[2][NW];
     __shared__ int s_piv[B];
     const int r = threadIdx.x, lane = r & 31, w = r >> 5;
@@ -776,7 +1142,7 @@ __global__ void __launch_bounds__((B + 31) / 32 * 32) k_factor_diag_rows(const i
     int mystep = 0;
     bool bad = false;
     {
-        const unsigned long long key = warp_max_u64(used ? 0ull : gjr_key<C>(A[0], r));
+        const unsigned long long key = warp_pivot_key<C>(A[0], used, r);
         if (lane == 0) s_key[0][w] = key;
     }
     __syncthreads();
@@ -794,10 +1160,20 @@ __global__ void __launch_bounds__((B + 31) / 32 * 32) k_factor_diag_rows(const i
         if (r == p) {
             const C pinv = C(1) / (zero ? C(1) : A[k]);
 #pragma unroll
-            for (int c = 0; c < B; ++c) {
-                const C v = c == k ? pinv : A[c] * pinv;
-                s_prow[buf][c] = v;
-                A[c] = v;
+            for (int c0 = 0; c0 < BP; c0 += VW) {
+                C pr[VW];
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {
+                    const int c = c0 + u;
+                    if (c < B) {
+                        const C v = c == k ? pinv : A[c] * pinv;
+                        pr[u] = v;
+                        A[c] = v;
+                    } else {
+                        pr[u] = C(0);
+                    }
+                }
+                Vec16<C>::st(&s_prow[buf][c0], pr);
             }
             used = true;
             mystep = k;
@@ -807,12 +1183,19 @@ __global__ void __launch_bounds__((B + 31) / 32 * 32) k_factor_diag_rows(const i
         if (act && r != p) {
             const C f = A[k];
 #pragma unroll
-            for (int c = 0; c < B; ++c)
-                if (c != k) A[c] = fma_rn(-f, s_prow[buf][c], A[c]);
+            for (int c0 = 0; c0 < BP; c0 += VW) {
+                C pr[VW];
+                Vec16<C>::ld(pr, &s_prow[buf][c0]);
+#pragma unroll
+                for (int u = 0; u < VW; ++u) {
+                    const int c = c0 + u;
+                    if (c < B && c != k) A[c] = fma_rn(-f, pr[u], A[c]);
+                }
+            }
             A[k] = -f * s_prow[buf][k];
         }
         if (k + 1 < B) {
-            const unsigned long long key = warp_max_u64(used ? 0ull : gjr_key<C>(A[k + 1], r));
+            const unsigned long long key = warp_pivot_key<C>(A[k + 1], used, r);
             if (lane == 0) s_key[buf ^ 1][w] = key;
         }
         __syncthreads();
@@ -950,6 +1333,115 @@ __global__ void __launch_bounds__(256) k_sweep_bwd_shared(const int *rows0, int 
         const C v = block_col_dot<C>(dinv + (long long)R * bb + a, t + (g * s + k) * b, b);
         y[voff[R] + a] = v;
         AR::st(z + voff[R] + a, CT<C>::template to_vec<AR>(v));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Two-colour application (Sec. 4.2.1 sweeps on a bipartite block pattern):
+// when the lower DAG has two levels, the rows of its second level have no
+// upper entries and those of the first no lower entries, the two sweeps
+// reduce to
+//   K1, second-colour rows:  y_R = v_R - sum_p L_p v_col,  z_R = D_R^{-1} y_R
+//   K2, first-colour rows:   z_R = D_R^{-1} (v_R - sum_p U_p z_col)
+// since y = v on the first colour and z_R needs only y_R on the second.  Two
+// launches instead of four, and neither y_A nor y_B goes through memory.  The
+// block size is a compile-time constant: each block's B column loads are
+// issued at once, and every dot product keeps block_col_dot's arithmetic
+// (even columns into one accumulator, odd into the other, in column order,
+// explicit fma), so the application is bitwise that of the level sweeps.
+template <class C, class F, int B, class XF>
+__device__ __forceinline__ C block_col_dot_b(const F *Bp, XF x) {
+    C bv[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) bv[c] = (C)ldfac(Bp + c * B);
+    C s0 = C(0), s1 = C(0);
+#pragma unroll
+    for (int c = 0; c < B; c += 2) {
+        s0 = fma_rn(bv[c], x(c), s0);
+        if (c + 1 < B) s1 = fma_rn(bv[c + 1], x(c + 1), s1);
+    }
+    return s0 + s1;
+}
+
+template <class AR, class C, class F, int B>
+__global__ void __launch_bounds__(256) k_sweep_fd(const int *rows, int nrows, const int *rp, const int *ci,
+                                                  const int *voff, const F *vals, const F *dinv, const vec8 *v,
+                                                  C *y, vec8 *z) {
+    constexpr int G = 256 / B;
+    constexpr long long BB = (long long)B * B;
+    __shared__ C t[G * B];
+    const int g = threadIdx.x / B, a = threadIdx.x - g * B;
+    const int idx = blockIdx.x * G + g;
+    const bool active = (g < G) && (idx < nrows);
+    int R = 0;
+    if (active) {
+        R = rows[idx];
+        C acc = CT<C>::template from_vec<AR>(AR::ld(v + voff[R] + a));
+        for (int p = rp[R]; p < rp[R + 1]; ++p) {
+            const int col = ci[p];
+            if (col >= R) break;
+            const vec8 *xv = v + voff[col];  // y_col = v_col: a row without lower entries
+            acc -= block_col_dot_b<C, F, B>(vals + p * BB + a,
+                                            [&](int c) { return CT<C>::template from_vec<AR>(AR::ld(xv + c)); });
+        }
+        t[g * B + a] = acc;
+    }
+    __syncthreads();
+    if (!active) return;
+    const C *tg = t + g * B;
+    const C zv = block_col_dot_b<C, F, B>(dinv + R * BB + a, [&](int c) { return tg[c]; });
+    y[voff[R] + a] = zv;
+    AR::st(z + voff[R] + a, CT<C>::template to_vec<AR>(zv));
+}
+
+// K2 with the upper blocks shared by the S stages (-dt J_ij for every stage):
+// one group per first-colour element, each upper block read once.
+template <class AR, class C, class F, int S, int B>
+__global__ void __launch_bounds__(256) k_sweep_bu(const int *rows0, int nrows, int T, const int *rp, const int *ci,
+                                                  const int *voff, const F *vals, const F *dinv, const vec8 *v,
+                                                  C *y, vec8 *z) {
+    constexpr int G = 256 / B;
+    constexpr long long BB = (long long)B * B;
+    __shared__ C t[G * S * B];
+    const int g = threadIdx.x / B, a = threadIdx.x - g * B;
+    const int idx = blockIdx.x * G + g;
+    const bool active = (g < G) && (idx < nrows);
+    int R0 = 0;
+    if (active) {
+        R0 = rows0[idx];
+        C acc[S];
+#pragma unroll
+        for (int k = 0; k < S; ++k) acc[k] = CT<C>::template from_vec<AR>(AR::ld(v + voff[k * T + R0] + a));
+        for (int p = rp[R0 + 1] - 1; p >= rp[R0]; --p) {
+            const int col = ci[p];
+            if (col <= R0) break;
+            C bv[B];
+#pragma unroll
+            for (int c = 0; c < B; ++c) bv[c] = (C)ldfac(vals + p * BB + a + c * B);
+#pragma unroll
+            for (int k = 0; k < S; ++k) {
+                const C *x = y + voff[k * T + col];
+                C s0 = C(0), s1 = C(0);
+#pragma unroll
+                for (int c = 0; c < B; c += 2) {
+                    s0 = fma_rn(bv[c], x[c], s0);
+                    if (c + 1 < B) s1 = fma_rn(bv[c + 1], x[c + 1], s1);
+                }
+                acc[k] -= s0 + s1;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < S; ++k) t[(g * S + k) * B + a] = acc[k];
+    }
+    __syncthreads();
+    if (!active) return;
+#pragma unroll
+    for (int k = 0; k < S; ++k) {
+        const int R = k * T + R0;
+        const C *tk = t + (g * S + k) * B;
+        const C zv = block_col_dot_b<C, F, B>(dinv + R * BB + a, [&](int c) { return tk[c]; });
+        y[voff[R] + a] = zv;
+        AR::st(z + voff[R] + a, CT<C>::template to_vec<AR>(zv));
     }
 }
 
@@ -1484,6 +1976,36 @@ int pc_build_pattern(irk_ctx *c) {
             }
         }
     }
+    P.two_colour = 0;
+    if (h.lo_ptr.size() == 3 && h.up_ptr.size() == 3 &&
+        (h.lo_ptr[2] - h.lo_ptr[1]) + (h.up_ptr[2] - h.up_ptr[1]) == h.nb) {
+        bool ok = true;
+        for (int q = h.lo_ptr[1]; q < h.lo_ptr[2] && ok; ++q) {
+            const int R = h.lo_rows[q];
+            if (h.ci[h.rp[R + 1] - 1] > R) ok = false;  // an upper entry
+        }
+        for (int q = h.up_ptr[1]; q < h.up_ptr[2] && ok; ++q) {
+            const int R = h.up_rows[q];
+            if (h.ci[h.rp[R]] < R) ok = false;  // a lower entry
+        }
+        P.two_colour = ok ? 1 : 0;
+    }
+    // does every update of a lower entry land on its row's diagonal block (a
+    // single update each: no two lower neighbours of a row adjacent)?
+    P.fused_r = 0;
+    {
+        bool diag_only = true;
+        int rmax = 0;
+        for (int R = 0; R < h.nb && diag_only; ++R) {
+            int r = 0;
+            for (int p = h.rp[R]; p < h.rp[R + 1] && h.ci[p] < R; ++p) {
+                ++r;
+                if (h.upd_ptr[p + 1] - h.upd_ptr[p] != 1 || h.upd[2 * h.upd_ptr[p]] != h.diag[R]) diag_only = false;
+            }
+            rmax = std::max(rmax, r);
+        }
+        if (diag_only) P.fused_r = rmax;
+    }
     P.nb = h.nb;
     P.b = h.b;
     P.nnz = (long long)h.ci.size();
@@ -1566,6 +2088,57 @@ static bool launch_diag_rows(cudaStream_t st, int n, int b, const int *rows, con
     }
 }
 
+// Warps per CTA of k_factor_fused for this pattern (8 or 16), or 0 when it
+// does not apply: updates not diagonal-only, odd block size (bulk copies want
+// 16-byte multiples), more phase-1 tiles than the warps' registers hold, or
+// the row's blocks do not fit in shared memory.  IRK_NO_FUSED_FACTOR turns it
+// off.
+static size_t fused_smem(const PcSystem &P) {
+    const size_t stride = ((size_t)P.b * P.b * 4 + 127) / 128 * 128;
+    return stride * (1 + 3 * (size_t)P.fused_r) + 128;
+}
+static int fused_warps(const PcSystem &P) {
+    if (P.fused_r <= 0 || (P.b & 1) || getenv("IRK_NO_FUSED_FACTOR") != nullptr) return 0;
+    if (fused_smem(P) > 227 * 1024) return 0;
+    const int items = P.fused_r * ((P.b + 15) / 16) * ((P.b + 7) / 8);
+    if (items <= 8 * IRK_FUSED_TPW) return 8;
+    if (items <= 16 * IRK_FUSED_TPW) return 16;
+    return 0;
+}
+// Compile-time block sizes of k_factor_fused_b (the sizes of the workloads);
+// other even sizes take the generic k_factor_fused.
+template <int B>
+static bool launch_fused_b(int n, size_t smem, cudaStream_t st, const int *rows, const PcSystem &P, float *vals,
+                           const float *dinv, int *err) {
+    if (P.b != B) return false;
+    const int mt = (B + 15) / 16;
+    const int nw = std::max(1, std::min(16, P.fused_r * mt));
+    allow_max_smem((const void *)k_factor_fused_b<B>);
+    k_factor_fused_b<B><<<n, 32 * nw, smem, st>>>(rows, P.d_rp, P.d_ci, P.d_diag, P.d_upd_ptr, P.d_upd, vals, dinv,
+                                                 P.fused_r, err);
+    return true;
+}
+
+static void launch_fused(int nw, int n, size_t smem, cudaStream_t st, const int *rows, const PcSystem &P,
+                         float *vals, const float *dinv, int *err) {
+    if (getenv("IRK_FUSED_GENERIC") == nullptr &&
+        (launch_fused_b<40>(n, smem, st, rows, P, vals, dinv, err) ||
+         launch_fused_b<50>(n, smem, st, rows, P, vals, dinv, err) ||
+         launch_fused_b<24>(n, smem, st, rows, P, vals, dinv, err) ||
+         launch_fused_b<20>(n, smem, st, rows, P, vals, dinv, err) ||
+         launch_fused_b<12>(n, smem, st, rows, P, vals, dinv, err)))
+        return;
+    if (nw == 8) {
+        allow_max_smem((const void *)k_factor_fused<8>);
+        k_factor_fused<8><<<n, 256, smem, st>>>(rows, P.b, P.d_rp, P.d_ci, P.d_diag, P.d_upd_ptr, P.d_upd, vals,
+                                                dinv, P.fused_r, err);
+    } else {
+        allow_max_smem((const void *)k_factor_fused<16>);
+        k_factor_fused<16><<<n, 512, smem, st>>>(rows, P.b, P.d_rp, P.d_ci, P.d_diag, P.d_upd_ptr, P.d_upd, vals,
+                                                 dinv, P.fused_r, err);
+    }
+}
+
 template <class C>
 static int factor_impl(irk_ctx *c, double dt) {
     PcSystem &P = c->pc;
@@ -1608,22 +2181,32 @@ static int factor_impl(irk_ctx *c, double dt) {
     allow_max_smem((const void *)k_factor_level<C>);
     allow_max_smem((const void *)k_factor_diag<C>);
     const int nlev = (int)P.lo_ptr.size() - 1;
+    c->stats.factor_fused_levels = 0;
+    // staged whole-row products (binary32 factors, diagonal-only updates)
+    const int fused_nw = std::is_same<C, float>::value ? fused_warps(P) : 0;
+    const size_t smem_f = fused_smem(P);
     // inversions in their own small CTAs: every row of level 0 (no lower
     // entries: nothing to update), and the rows of levels with at least
     // split_min rows after their products (one more launch per level)
     const int gjt = std::max(gj_threads(), (b + 31) / 32 * 32);
+    const int split_min = gj_split_min();
     const size_t smem_d = ((size_t)2 * b * b + (size_t)2 * b) * sizeof(C);
     for (int l = 0; l < nlev; ++l) {
         int n = P.lo_ptr[l + 1] - P.lo_ptr[l];
         if (n <= 0) continue;
         const int *lrows = P.d_lo_rows + P.lo_ptr[l];
         if (fast) {
-            const bool split = l == 0 || n >= gj_split_min();
+            const bool split = l == 0 || n >= split_min;
             if (l > 0) {
                 tm = tmark_begin(c);
-                k_factor_level2<C><<<n, 256, smem4, c->stream>>>(lrows, b, P.d_rp, P.d_ci, P.d_diag, P.d_upd_ptr,
-                                                                 P.d_upd, (C *)P.d_vals, (C *)P.d_dinv, c->d_err,
-                                                                 split ? 0 : 1);
+                if (split && fused_nw > 0) {
+                    launch_fused(fused_nw, n, smem_f, c->stream, lrows, P, (float *)P.d_vals, (const float *)P.d_dinv,
+                                 c->d_err);
+                    c->stats.factor_fused_levels++;
+                } else
+                    k_factor_level2<C><<<n, 256, smem4, c->stream>>>(lrows, b, P.d_rp, P.d_ci, P.d_diag,
+                                                                     P.d_upd_ptr, P.d_upd, (C *)P.d_vals,
+                                                                     (C *)P.d_dinv, c->d_err, split ? 0 : 1);
                 tmark_end(c, tm, 4);
             }
             if (split) {
@@ -1694,11 +2277,61 @@ static int apply_persistent(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, c
     return cuda_status(e);
 }
 
+// The two-colour application (k_sweep_fd, k_sweep_bu) for block size B.
+template <class AR, class C, class F, int B>
+static bool apply_two_colour(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv) {
+    PcSystem &P = c->pc;
+    if (P.b != B) return false;
+    constexpr int G = 256 / B;
+    const int threads = (G * B + 31) / 32 * 32;
+    C *y = (C *)P.d_y;
+    int tm = tmark_begin(c);
+    const int n1 = P.lo_ptr[2] - P.lo_ptr[1];
+    if (n1 > 0) {
+        k_sweep_fd<AR, C, F, B><<<(n1 + G - 1) / G, threads, 0, c->stream>>>(
+            P.d_lo_rows + P.lo_ptr[1], n1, P.d_rp, P.d_ci, P.d_voff, vals, dinv, v, y, z);
+        c->launches++;
+    }
+    tmark_end(c, tm, 6);
+    tm = tmark_begin(c);
+    const int s = c->s;
+    if (P.shared_upper && s >= 2 && s <= 4 && getenv("IRK_NO_SHARED_UPPER") == nullptr) {
+        const int n2 = P.up0_ptr[2] - P.up0_ptr[1];
+        auto kern = s == 2 ? k_sweep_bu<AR, C, F, 2, B>
+                           : (s == 3 ? k_sweep_bu<AR, C, F, 3, B> : k_sweep_bu<AR, C, F, 4, B>);
+        if (n2 > 0) {
+            kern<<<(n2 + G - 1) / G, threads, 0, c->stream>>>(P.d_up0_rows + P.up0_ptr[1], n2, c->T, P.d_rp, P.d_ci,
+                                                               P.d_voff, vals, dinv, v, y, z);
+            c->launches++;
+        }
+    } else {
+        const int n2 = P.up_ptr[2] - P.up_ptr[1];
+        if (n2 > 0) {
+            k_sweep_bu<AR, C, F, 1, B><<<(n2 + G - 1) / G, threads, 0, c->stream>>>(
+                P.d_up_rows + P.up_ptr[1], n2, c->T, P.d_rp, P.d_ci, P.d_voff, vals, dinv, v, y, z);
+            c->launches++;
+        }
+    }
+    tmark_end(c, tm, 7);
+    c->stats.sweep_two_colour = 1;
+    return true;
+}
+
 template <class AR, class C, class F>
 static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv) {
     PcSystem &P = c->pc;
     const int b = P.b;
+    c->stats.sweep_two_colour = 0;
     if (P.persistent) return apply_persistent<AR, C, F>(c, v, z, vals, dinv);
+    if constexpr (std::is_same<C, float>::value && std::is_same<AR, ArDF>::value) {
+        if (P.two_colour && getenv("IRK_NO_TWO_COLOUR") == nullptr &&
+            (apply_two_colour<AR, C, F, 40>(c, v, z, vals, dinv) ||
+             apply_two_colour<AR, C, F, 50>(c, v, z, vals, dinv) ||
+             apply_two_colour<AR, C, F, 24>(c, v, z, vals, dinv) ||
+             apply_two_colour<AR, C, F, 20>(c, v, z, vals, dinv) ||
+             apply_two_colour<AR, C, F, 12>(c, v, z, vals, dinv)))
+            return cuda_status(cudaGetLastError());
+    }
     const int groups = std::max(1, 256 / b);
     const int threads = (groups * b + 31) / 32 * 32;
     C *y = (C *)P.d_y;

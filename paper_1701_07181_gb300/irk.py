@@ -52,7 +52,8 @@ class Stats(ctypes.Structure):
                 ("n_matvec", ctypes.c_int), ("n_precond", ctypes.c_int), ("n_ortho", ctypes.c_int),
                 ("matvec_variant", ctypes.c_int), ("factor_assemble_ms", ctypes.c_double),
                 ("factor_products_ms", ctypes.c_double), ("factor_inverse_ms", ctypes.c_double),
-                ("sweep_fwd_ms", ctypes.c_double), ("sweep_bwd_ms", ctypes.c_double)]
+                ("sweep_fwd_ms", ctypes.c_double), ("sweep_bwd_ms", ctypes.c_double),
+                ("factor_fused_levels", ctypes.c_int), ("sweep_two_colour", ctypes.c_int)]
 
 
 EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor", "irk_solve",

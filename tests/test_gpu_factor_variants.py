@@ -67,3 +67,61 @@ def test_singular_block_reported(monkeypatch, rows):
         with pytest.raises(irk.IrkError) as e:
             S.factor(0.5)
     assert e.value.code == -3
+
+
+def _mesh(kind):
+    return {"2d": inputs.mesh_2d_periodic(7, 5), "3d": inputs.mesh_3d_periodic(3, 4, 3),
+            "chain": inputs.mesh_1d_chain(37)}[kind]
+
+
+@pytest.mark.parametrize("kind,s,m,order", [("2d", 3, 40, "multicolor"), ("2d", 2, 12, "natural"),
+                                            ("3d", 2, 20, "multicolor"), ("3d", 3, 50, "multicolor"),
+                                            ("chain", 1, 24, "natural"), ("2d", 2, 16, "multicolor")])
+def test_fused_products_match_per_entry_kernel(monkeypatch, kind, s, m, order):
+    """Whole-row staged products (every update of a lower block lands on the
+    row's diagonal block: no three elements pairwise adjacent in these
+    meshes), in the compile-time block-size form (m = 12, 20, 24, 40, 50;
+    m = 16 takes the generic form) and the generic form (IRK_FUSED_GENERIC),
+    against the per-entry product kernel, every level through the separate
+    inversion kernel: they differ only in the summation order of the Schur
+    update, so their preconditioner applications agree to binary32 rounding;
+    with double-float Krylov the fused factors also reach rtol 1e-8."""
+    irk = _irk()
+    monkeypatch.setenv("IRK_GJ_SPLIT_MIN", "1")
+    P = inputs.make_problem(_mesh(kind), m, s, 0.3, 4.0, seed=5)
+    V = np.random.default_rng(4).standard_normal(P.s * P.T * P.m)
+    out, fused = [], []
+    for mode in ("compiled", "generic", "off"):
+        if mode == "generic":
+            monkeypatch.setenv("IRK_FUSED_GENERIC", "1")
+        if mode == "off":
+            monkeypatch.setenv("IRK_NO_FUSED_FACTOR", "1")
+        with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, precond="uncoupled", factor_prec="fp32",
+                        krylov="df64", ordering=order) as S:
+            S.factor(0.3)
+            out.append(S.apply_precond(V))
+            fused.append(S.stats()["factor_fused_levels"])
+            if mode != "off":
+                W, it, rr, rc = S.solve(P.R, 0.3, rtol=1e-8)
+                assert rc == 0 and rr <= 1e-8
+                ref = oracle.Problem(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M)
+                assert np.linalg.norm(P.R - ref.apply(W, 0.3)) / np.linalg.norm(P.R) <= 1e-8
+    assert fused[0] >= 1 and fused[1] == fused[0] and fused[2] == 0
+    assert rel(out[0], out[2]) <= 1e-5
+    assert rel(out[1], out[2]) <= 1e-5
+
+
+def test_coupled_preconditioner_keeps_per_entry_kernel(monkeypatch):
+    """With three stages the stage blocks of one element are pairwise coupled
+    in the stage-coupled preconditioner, so a row's stage-0 and stage-1 lower
+    entries are adjacent, updates reach off-diagonal blocks and the
+    staged-row kernel must not be chosen."""
+    irk = _irk()
+    monkeypatch.setenv("IRK_GJ_SPLIT_MIN", "1")
+    P = inputs.make_problem(_mesh("2d"), 12, 3, 0.3, 4.0, seed=5)
+    with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, precond="coupled", factor_prec="fp32",
+                    krylov="df64", ordering="multicolor") as S:
+        S.factor(0.3)
+        assert S.stats()["factor_fused_levels"] == 0
+        W, it, rr, rc = S.solve(P.R, 0.3, rtol=1e-8)
+    assert rc == 0 and rr <= 1e-8

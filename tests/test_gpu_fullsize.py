@@ -78,6 +78,8 @@ def test_c1_solve_full_size(c1, c1_solver, dt):
     P = c1
     W, it, rr, rc = c1_solver.solve(dev(P.R), dt, rtol=1e-8)
     assert rc == 0 and rr <= 1e-8
+    # the second colour level's products ran as staged whole rows
+    assert c1_solver.stats()["factor_fused_levels"] == 1
     W = W.cpu().numpy()
     ref = oracle.Problem(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M)
     res = np.linalg.norm(P.R - ref.apply(W, dt)) / np.linalg.norm(P.R)

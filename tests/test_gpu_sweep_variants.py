@@ -55,3 +55,44 @@ def test_mutual_neighbours_fall_back_and_match_oracle():
             S.factor(0.4)
             z = S.apply_precond(V)
         assert np.linalg.norm(z - ref) <= 1e-11 * np.linalg.norm(ref)
+
+
+@pytest.mark.parametrize("fprec", ["fp32", "bf16"])
+@pytest.mark.parametrize("kind,s,m,shared", [("2d", 3, 40, True), ("3d", 2, 20, True), ("2d", 4, 12, True),
+                                             ("3d", 3, 50, True), ("chain", 1, 24, True), ("2d", 3, 40, False)])
+def test_two_colour_application_is_bitwise_equal(monkeypatch, fprec, kind, s, m, shared):
+    """In the two-colour order the first colour's rows have no lower entries
+    (y = v there) and the second colour's no upper entries (z = D^{-1} y right
+    after the forward row), so the application runs as two launches instead
+    of four.  It keeps every dot product's arithmetic: the preconditioned
+    vector and a whole FGMRES solve are bitwise equal to the level sweeps'
+    (IRK_NO_TWO_COLOUR=1), with two launches fewer per application.  Shared
+    upper blocks for all stages, and per-stage upper blocks (s = 1, and
+    IRK_NO_SHARED_UPPER=1).  The Kuhn-tetrahedra meshes need four colours
+    in first-fit order: there the level sweeps run either way."""
+    irk = _irk()
+    nb = {"2d": inputs.mesh_2d_periodic(9, 7), "3d": inputs.mesh_3d_periodic(3, 3, 4),
+          "chain": inputs.mesh_1d_chain(38)}[kind]
+    if not shared:
+        monkeypatch.setenv("IRK_NO_SHARED_UPPER", "1")
+    P = inputs.make_problem(nb, m, s, 0.3, 4.0, seed=2)
+    V = np.random.default_rng(8).standard_normal(P.s * P.T * P.m)
+    out, sol, launches = [], [], []
+    for off in ("", "1"):
+        if off:
+            monkeypatch.setenv("IRK_NO_TWO_COLOUR", "1")
+        with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec=fprec, krylov="df64",
+                        sweep="levels", ordering="multicolor", timing=True) as S:
+            S.factor(0.3)
+            out.append(S.apply_precond(V))
+            W, it, rr, rc = S.solve(P.R, 0.3, rtol=1e-8)
+            assert rc == 0 and rr <= 1e-8
+            st = S.stats()
+            sol.append((W, it))
+            launches.append((st["kernel_launches"], st["n_precond"]))
+            assert st["sweep_two_colour"] == (1 if (not off and kind != "3d") else 0)
+    np.testing.assert_array_equal(out[0], out[1])
+    np.testing.assert_array_equal(sol[0][0], sol[1][0])
+    assert sol[0][1] == sol[1][1]
+    two_colour = kind != "3d"
+    assert launches[1][0] - launches[0][0] == (2 * launches[0][1] if two_colour else 0)
