@@ -129,7 +129,13 @@ typedef struct {
                             copied at irk_setup */
     void *stream;      /* cudaStream_t for all work of the context; NULL = default */
     int timing;        /* 1: time each phase of irk_factor / irk_solve with CUDA
-                          events on the context's stream (see irk_stats); default 0 */
+                          events on the context's stream (see irk_stats); the
+                          events are read back at the end of each call.
+                          2: the same events, left unread until irk_get_stats,
+                          which then reports the phase times, phase counts
+                          and kernel launches summed over every irk_factor /
+                          irk_solve since the previous irk_get_stats call (no
+                          event query on the solve's path).  Default 0 */
     int sweep;         /* enum irk_sweep_mode: how the preconditioner sweeps run */
     int ordering;      /* enum irk_ordering: elimination order of the ILU(0) */
     int partitions;    /* > 1: partitioned ILU(0) (Sec. 4.5) with this many
@@ -335,9 +341,11 @@ IRK_API void irk_dirk_destroy(irk_dirk *d);
 typedef struct {
     int iters, cycles, levels_lower, levels_upper;
     double relres, factor_ms, solve_ms;
-    long long kernel_launches;  /* kernels launched by the last factor + solve */
+    long long kernel_launches;  /* kernels launched by the last factor + solve
+                                   (timing = 2: since the previous irk_get_stats) */
     /* with irk_options.timing = 1 (else 0): device time of each phase of the
-     * last irk_solve, summed over its calls, from CUDA events on the stream */
+     * last irk_solve, summed over its calls, from CUDA events on the stream
+     * (timing = 2: over every call since the previous irk_get_stats) */
     double matvec_ms, precond_ms, ortho_ms;
     int n_matvec, n_precond, n_ortho;
     /* launch variant of the operator product chosen by the autotuner for this
@@ -346,8 +354,9 @@ typedef struct {
      * (2 or 3 shared-memory stages, one or two CTAs per SM; where a stage does
      * not fit or m is odd it runs variant 0's launch), 7 register-streaming
      * kernel with the block size fixed at compile time (double-float Krylov,
-     * s = 2..4, m = 12, 20, 24, 40 or 50; else variant 0's launch); -1 before
-     * the first product.  The environment variable IRK_MATVEC_VARIANT=<0..7>, read when
+     * s = 2..4, m = 12, 20, 24, 40 or 50; else variant 0's launch), 8 the
+     * same register-blocked (four rows per thread, two for m = 50); -1 before
+     * the first product.  The environment variable IRK_MATVEC_VARIANT=<0..8>, read when
      * a context makes its first product, pins the variant.  Every variant
      * gives the same result bit for bit. */
     int matvec_variant;

@@ -185,8 +185,19 @@ int load_values(irk_ctx *c, const double *J, const double *M, int mem_space) {
 // phase of kind 0 (operator product), 1 (preconditioner), 2 (Gram-Schmidt),
 // 3 (factor assembly), 4 (factor block products), 5 (factor inverses),
 // 6 (forward sweep), 7 (backward sweep).
+#define IRK_TMARK_FLUSH 32768
+
+namespace {
+void tflush(irk_ctx *c);
+}
+
 int tmark_begin(irk_ctx *c) {
     if (!c->opt.timing) return -1;
+    if (c->opt.timing == 2 && c->tused >= 2 * IRK_TMARK_FLUSH) {
+        // bound the pending marks of a caller that never asks for stats
+        cudaStreamSynchronize(c->stream);
+        tflush(c);
+    }
     if (c->tused + 2 > (int)c->tev.size()) {
         for (int q = 0; q < 64; ++q) {
             cudaEvent_t e;
@@ -225,6 +236,36 @@ void tcollect(irk_ctx *c) {
         }
     }
     c->tused = 0;
+}
+
+// timing = 2: read every pending mark into the running totals (by kind) and
+// release the marks; the caller has synchronised the stream
+void tflush(irk_ctx *c) {
+    for (int slot = 0; slot < c->tused; slot += 2) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, c->tev[slot], c->tev[slot + 1]);
+        const int k = c->tkind[slot / 2] & 7;
+        c->tacc_ms[k] += ms;
+        c->tacc_n[k]++;
+    }
+    c->tused = 0;
+}
+
+// timing = 2: the totals since the last irk_get_stats into the phase fields
+// (kind 0 operator product, 1 preconditioner, 2 orthogonalisation, 3-5
+// factorisation kernels, 6-7 sweeps), then cleared
+void treport(irk_ctx *c) {
+    tflush(c);
+    irk_stats &t = c->stats;
+    t.matvec_ms = c->tacc_ms[0], t.n_matvec = c->tacc_n[0];
+    t.precond_ms = c->tacc_ms[1], t.n_precond = c->tacc_n[1];
+    t.ortho_ms = c->tacc_ms[2], t.n_ortho = c->tacc_n[2];
+    t.factor_assemble_ms = c->tacc_ms[3];
+    t.factor_products_ms = c->tacc_ms[4];
+    t.factor_inverse_ms = c->tacc_ms[5];
+    t.sweep_fwd_ms = c->tacc_ms[6];
+    t.sweep_bwd_ms = c->tacc_ms[7];
+    for (int k = 0; k < 8; ++k) c->tacc_ms[k] = 0.0, c->tacc_n[k] = 0;
 }
 
 // the factorisation's marks (kinds 3-5), collected after its synchronisation
@@ -465,27 +506,39 @@ int irk_update_values(irk_ctx *c, const double *J, const double *M, int mem_spac
     return load_values(c, J, M, mem_space);
 }
 
-int irk_factor(irk_ctx *c, double dt) {
-    if (!c || !std::isfinite(dt)) return IRK_ERR_INVALID;
-    cudaEvent_t e0, e1;
-    cudaEventCreate(&e0);
-    cudaEventCreate(&e1);
-    long long l0 = c->launches;
-    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
-    c->tused = 0;
+// The factorisation's launches between two events; the caller synchronises
+// (the error word must be clear before) and then calls factor_finish.
+static int factor_enqueue(irk_ctx *c, double dt, cudaEvent_t e0, cudaEvent_t e1) {
+    if (c->opt.timing != 2) c->tused = 0;
     cudaEventRecord(e0, c->stream);
-    int rc = pc_factor(c, dt);
+    const int rc = pc_factor(c, dt);
     cudaEventRecord(e1, c->stream);
-    if (rc == IRK_OK) rc = sync_err(c);
+    return rc;
+}
+
+// After a synchronisation covering the factorisation; rc is its outcome.
+static void factor_finish(irk_ctx *c, double dt, int rc, cudaEvent_t e0, cudaEvent_t e1, long long l0) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
-    tcollect_factor(c);
+    if (c->opt.timing != 2) tcollect_factor(c);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->stats.factor_ms = ms;
     c->stats.kernel_launches = c->launches - l0;
     c->factored = (rc == IRK_OK);
     c->factored_dt = dt;
+}
+
+int irk_factor(irk_ctx *c, double dt) {
+    if (!c || !std::isfinite(dt)) return IRK_ERR_INVALID;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const long long l0 = c->launches;
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    int rc = factor_enqueue(c, dt, e0, e1);
+    if (rc == IRK_OK) rc = sync_err(c);
+    factor_finish(c, dt, rc, e0, e1, l0);
     return rc;
 }
 
@@ -519,18 +572,28 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     if (!c || !Rhs || !W || !(rtol >= 0.0) || !std::isfinite(dt)) return IRK_ERR_INVALID;
     int rc;
     const long long l0 = c->launches;  // counts the refactorisation too, if any
-    if (c->opt.precond != IRK_PC_NONE && (!c->factored || c->factored_dt != dt)) {
-        if ((rc = irk_factor(c, dt))) return rc;
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
+    cudaMemsetAsync(c->d_gbar, 0, 2 * sizeof(unsigned int), c->stream);
+    // a refactorisation is enqueued ahead of the solve; the synchronisation
+    // that reads ||R|| below also reports its errors (no round trip of its own)
+    const bool refactor = c->opt.precond != IRK_PC_NONE && (!c->factored || c->factored_dt != dt);
+    cudaEvent_t fe0 = nullptr, fe1 = nullptr;
+    if (refactor) {
+        cudaEventCreate(&fe0);
+        cudaEventCreate(&fe1);
+        if ((rc = factor_enqueue(c, dt, fe0, fe1))) {
+            cudaStreamSynchronize(c->stream);
+            factor_finish(c, dt, rc, fe0, fe1, l0);
+            return rc;
+        }
     }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventRecord(e0, c->stream);
-    c->tused = 0;
+    if (c->opt.timing != 2 && !refactor) c->tused = 0;
     const long long N = c->N;
     const int Rs = c->opt.restart;
-    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
-    cudaMemsetAsync(c->d_gbar, 0, 2 * sizeof(unsigned int), c->stream);
     double *est_h = c->h_scal, *beta_h = c->h_scal + 1, *hn_h = c->h_scal + 2;
     int total = 0, cycles = 0;
     double bnorm = 0.0, beta = 0.0;
@@ -539,16 +602,35 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     if (!rc) rc = launch_axpy_dot_slot(c, c->d_b, nullptr, 0, nullptr, 1, 1, 0, nullptr);
     if (!rc) rc = cuda_status(cudaMemcpyAsync(beta_h, irk_beta_ptr(c), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (!rc) rc = sync_err(c);
+    if (refactor) {
+        factor_finish(c, dt, rc, fe0, fe1, l0);
+        if (rc) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return rc;
+        }
+    }
     if (!rc) rc = launch_fill_zero(c, c->d_x, N);
     bnorm = *beta_h;
     if (!rc && !std::isfinite(bnorm)) rc = IRK_ERR_NONFINITE;
+    bool x_zero = true;
     while (rc == IRK_OK && bnorm > 0.0) {
         vec8 *V0 = c->d_V;
-        if ((rc = launch_matvec(c, c->d_x, V0, c->d_b, dt, 1))) break;
-        if ((rc = launch_axpy_dot_slot(c, V0, nullptr, 0, nullptr, 1, 1, 0, nullptr))) break;
-        cudaMemcpyAsync(beta_h, irk_beta_ptr(c), sizeof(double), cudaMemcpyDeviceToHost, c->stream);
-        if ((rc = sync_err(c))) break;
-        beta = *beta_h;
+        if (x_zero) {
+            // x = 0: the residual is R itself and its norm, in slot 0, is ||R||
+            // (the same kernel on the same data as the true-residual path)
+            if ((rc = cuda_status(
+                     cudaMemcpyAsync(V0, c->d_b, sizeof(vec8) * N, cudaMemcpyDeviceToDevice, c->stream))))
+                break;
+            beta = bnorm;
+            x_zero = false;
+        } else {
+            if ((rc = launch_matvec(c, c->d_x, V0, c->d_b, dt, 1))) break;
+            if ((rc = launch_axpy_dot_slot(c, V0, nullptr, 0, nullptr, 1, 1, 0, nullptr))) break;
+            cudaMemcpyAsync(beta_h, irk_beta_ptr(c), sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+            if ((rc = sync_err(c))) break;
+            beta = *beta_h;
+        }
         if (!std::isfinite(beta)) {
             rc = IRK_ERR_NONFINITE;
             break;
@@ -623,7 +705,7 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    tcollect(c);
+    if (c->opt.timing != 2) tcollect(c);
     c->stats.iters = total;
     c->stats.cycles = cycles;
     c->stats.relres = bnorm > 0.0 ? beta / bnorm : 0.0;
@@ -634,8 +716,18 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     return rc;
 }
 
-int irk_get_stats(const irk_ctx *c, irk_stats *out) {
-    if (!c || !out) return IRK_ERR_INVALID;
+int irk_get_stats(const irk_ctx *cc, irk_stats *out) {
+    if (!cc || !out) return IRK_ERR_INVALID;
+    if (cc->opt.timing == 2) {
+        // deferred marks: read every pending event pair now (the context's
+        // own timing state; the object itself is never const)
+        irk_ctx *c = const_cast<irk_ctx *>(cc);
+        cudaStreamSynchronize(c->stream);
+        treport(c);
+        c->stats.kernel_launches = c->launches - c->launches_at_stats;
+        c->launches_at_stats = c->launches;
+    }
+    const irk_ctx *c = cc;
     *out = c->stats;
     out->matvec_variant = c->mv_variant;
     return IRK_OK;

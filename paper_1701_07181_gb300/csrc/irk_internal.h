@@ -107,6 +107,12 @@ struct irk_ctx {
     int red_blocks = 0;
     irk_stats stats;
     long long launches = 0;
+    long long launches_at_stats = 0;  // timing = 2: launch count at the last irk_get_stats
+    // timing = 2: phase totals of the marks already read since the last
+    // irk_get_stats (marks are read when the stats are asked for, or when
+    // IRK_TMARK_FLUSH pairs are pending)
+    double tacc_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    int tacc_n[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     int mv_variant = -1;  // operator-product launch variant (autotuned on first use)
     // phase timing (irk_options.timing): event pool and (kind, start, end) marks
     std::vector<cudaEvent_t> tev;

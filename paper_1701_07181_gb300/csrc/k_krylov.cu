@@ -39,6 +39,19 @@ __device__ __forceinline__ typename AR::val block_reduce(typename AR::val v, typ
     return v;  // valid in thread 0
 }
 
+// Sum of the n per-CTA partials of a reduction by one warp: lane l adds
+// partials l, l + 32, ... in order, then a fixed shuffle tree; every CTA
+// computes the same value in the same order.  Valid in lane 0 (the other
+// lanes hold partial sums of the tree; only lane 0's result is used).
+template <class AR>
+__device__ __forceinline__ typename AR::val warp_sum_partials(const vec8 *pb, int n) {
+    typename AR::acc a = AR::zero();
+    for (int q = threadIdx.x & 31; q < n; q += 32) AR::add_to(a, AR::ldcg(pb + q));
+    typename AR::val v = AR::value(a);
+    for (int d = 16; d > 0; d >>= 1) v = AR::add(v, AR::shfl_down(v, d));
+    return v;
+}
+
 template <class AR>
 __device__ __forceinline__ typename AR::val scal_val(const Scal *s) {
     return AR::coef(s->d, s->hi, s->lo);
@@ -255,20 +268,20 @@ __global__ void __launch_bounds__(NT) k_arnoldi(long long N, int j, int R, vec8 
             if (blockIdx.x == 0 && threadIdx.x == 0) arnoldi_status(status, 0.0, 0.0, err);
             return;
         }
-        typename AR::acc a2 = AR::zero();
-        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) AR::add_to(a2, AR::ldcg(pb + q));
-        const val tot = block_reduce<AR>(AR::value(a2), sh);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
+            const val tot = warp_sum_partials<AR>(pb, (int)gridDim.x);
             double d = AR::to_double(tot);
             if (!isfinite(d)) {
-                if (blockIdx.x == 0) atomicOr(err, IRK_DEV_ERR_NONFINITE);
+                if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_NONFINITE);
                 d = 0.0;
             }
             if (last) d = d > 0.0 ? sqrt(d) : 0.0;
-            s_h = d;
-            if (blockIdx.x == 0) {
-                scal_store_d(slots + 2 + i, d);
-                H[i * R + j] = d;
+            if (threadIdx.x == 0) {
+                s_h = d;
+                if (blockIdx.x == 0) {
+                    scal_store_d(slots + 2 + i, d);
+                    H[i * R + j] = d;
+                }
             }
         }
         __syncthreads();
@@ -434,20 +447,20 @@ __global__ void __launch_bounds__(1024) k_arnoldi_smem(long long N, long long ch
             if (blockIdx.x == 0 && threadIdx.x == 0) arnoldi_status(status, 0.0, 0.0, err);
             return;
         }
-        typename AR::acc a2 = AR::zero();
-        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) AR::add_to(a2, AR::ldcg(pb + q));
-        const val tot = block_reduce<AR>(AR::value(a2), sh);
-        if (threadIdx.x == 0) {
+        if (threadIdx.x < 32) {
+            const val tot = warp_sum_partials<AR>(pb, (int)gridDim.x);
             double d = AR::to_double(tot);
             if (!isfinite(d)) {
-                if (blockIdx.x == 0) atomicOr(err, IRK_DEV_ERR_NONFINITE);
+                if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, IRK_DEV_ERR_NONFINITE);
                 d = 0.0;
             }
             if (last) d = d > 0.0 ? sqrt(d) : 0.0;
-            s_h = d;
-            if (blockIdx.x == 0) {
-                scal_store_d(slots + 2 + i, d);
-                H[i * R + j] = d;
+            if (threadIdx.x == 0) {
+                s_h = d;
+                if (blockIdx.x == 0) {
+                    scal_store_d(slots + 2 + i, d);
+                    H[i * R + j] = d;
+                }
             }
         }
         __syncthreads();

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "arith.cuh"
 #include "tma.cuh"
@@ -131,6 +132,125 @@ __global__ void __launch_bounds__(256) k_matvec(MatvecParams P) {
             accum_block<AR, S, CH>(t, P.J + (long long)p * mm + a, P.x + (long long)P.ci[p] * sm, m);
         if (P.form != IRK_FORM_JACOBIAN) accum_block<AR, S, CH>(z, P.M + i * mm + a, P.x + i * sm, m);
         store_row<AR, S>(P, i, a, t, z);
+    }
+}
+
+// The register-streaming product with the block size a compile-time constant
+// (double-float, the workloads' sizes): no bounds tests or 64-bit index
+// products per load, and a neighbour's stage values read two at a time with
+// 16-byte loads.  Every accumulator sees the same sequence of operations as
+// in k_matvec (block by block, column by column, stage by stage), so the
+// result is bitwise that of the other variants.
+template <int S, int B, int CH>
+__device__ __forceinline__ void accum_block_b(df_acc (&dst)[S], const vec8 *Bp, const vec8 *x) {
+#pragma unroll
+    for (int c0 = 0; c0 < B; c0 += CH) {
+        df64 bv[CH], xv[S][CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (c0 + u < B) bv[u] = ArDF::ld(Bp + (c0 + u) * B);
+#pragma unroll
+        for (int l = 0; l < S; ++l)
+#pragma unroll
+            for (int u = 0; u < CH; u += 2)
+                if (c0 + u < B) {  // B even: columns c0 + u and c0 + u + 1 together
+                    const float4 f = __ldg(reinterpret_cast<const float4 *>(x + l * B + c0 + u));
+                    xv[l][u] = df_make(f.x, f.y);
+                    xv[l][u + 1] = df_make(f.z, f.w);
+                }
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (c0 + u < B)
+#pragma unroll
+                for (int l = 0; l < S; ++l) ArDF::fma(dst[l], bv[u], xv[l][u]);
+    }
+}
+
+template <int S, int B, int CH>
+__global__ void __launch_bounds__(256) k_matvec_b(MatvecParams P) {
+    constexpr int G = 256 / B;
+    constexpr long long BB = (long long)B * B, SB = (long long)S * B;
+    const int g = threadIdx.x / B;
+    const int a = threadIdx.x - g * B;
+    if (g >= G) return;
+    for (long long i = (long long)blockIdx.x * G + g; i < P.T; i += (long long)gridDim.x * G) {
+        df_acc t[S], z[S];
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+            t[l] = ArDF::zero();
+            z[l] = ArDF::zero();
+        }
+        const int p0 = P.rp[i], p1 = P.rp[i + 1];
+        for (int p = p0; p < p1; ++p) accum_block_b<S, B, CH>(t, P.J + p * BB + a, P.x + P.ci[p] * SB);
+        if (P.form != IRK_FORM_JACOBIAN) accum_block_b<S, B, CH>(z, P.M + i * BB + a, P.x + i * SB);
+        store_row<ArDF, S>(P, i, a, t, z);
+    }
+}
+
+// Register-blocked form of k_matvec_b: a thread owns H pairs of adjacent rows
+// of the element row's blocks, rows h*(B/H) + 2q + {0, 1} (q its index in a
+// group of B/(2H) threads), so each block column arrives as H 16-byte loads
+// that are contiguous across the group, and each stage value of the
+// neighbour serves 2H rows.  Accumulator (row, stage) still sees blocks in
+// order and columns in order, as in every other variant.
+template <int S, int B, int H, int CH>
+__device__ __forceinline__ void accum_block_rb(df_acc (&dst)[2 * H][S], const vec8 *Bp, const vec8 *x, int q) {
+#pragma unroll
+    for (int c0 = 0; c0 < B; c0 += CH) {
+        df64 bv[CH][2 * H], xv[S][CH];
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+#pragma unroll
+            for (int h = 0; h < H; ++h)
+                if (c0 + u < B) {
+                    const float4 f =
+                        __ldg(reinterpret_cast<const float4 *>(Bp + (c0 + u) * B + h * (B / H) + 2 * q));
+                    bv[u][2 * h] = df_make(f.x, f.y);
+                    bv[u][2 * h + 1] = df_make(f.z, f.w);
+                }
+#pragma unroll
+        for (int l = 0; l < S; ++l)
+#pragma unroll
+            for (int u = 0; u < CH; u += 2)
+                if (c0 + u < B) {
+                    const float4 f = __ldg(reinterpret_cast<const float4 *>(x + l * B + c0 + u));
+                    xv[l][u] = df_make(f.x, f.y);
+                    xv[l][u + 1] = df_make(f.z, f.w);
+                }
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (c0 + u < B)
+#pragma unroll
+                for (int r = 0; r < 2 * H; ++r)
+#pragma unroll
+                    for (int l = 0; l < S; ++l) ArDF::fma(dst[r][l], bv[u][r], xv[l][u]);
+    }
+}
+
+template <int S, int B, int H, int CH>
+__global__ void __launch_bounds__(256) k_matvec_rb(MatvecParams P) {
+    constexpr int GT = B / (2 * H);  // threads per element row
+    constexpr int G = 256 / GT;
+    constexpr long long BB = (long long)B * B, SB = (long long)S * B;
+    const int g = threadIdx.x / GT;
+    const int q = threadIdx.x - g * GT;
+    if (g >= G) return;
+    for (long long i = (long long)blockIdx.x * G + g; i < P.T; i += (long long)gridDim.x * G) {
+        df_acc t[2 * H][S], z[2 * H][S];
+#pragma unroll
+        for (int r = 0; r < 2 * H; ++r)
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+                t[r][l] = ArDF::zero();
+                z[r][l] = ArDF::zero();
+            }
+        const int p0 = P.rp[i], p1 = P.rp[i + 1];
+        for (int p = p0; p < p1; ++p) accum_block_rb<S, B, H, CH>(t, P.J + p * BB, P.x + P.ci[p] * SB, q);
+        if (P.form != IRK_FORM_JACOBIAN) accum_block_rb<S, B, H, CH>(z, P.M + i * BB, P.x + i * SB, q);
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) store_row<ArDF, S>(P, i, h * (B / H) + 2 * q + j, t[2 * h + j], z[2 * h + j]);
     }
 }
 
@@ -425,15 +545,20 @@ int grid_for(long long work, int threads) {
 
 // Variants of the launch.  0-3: k_matvec with chunk width CH (columns whose
 // loads are in flight per thread) x threads per CTA.  4-6: k_matvec_pipe
-// with NS stages and the shared memory of one or two CTAs per SM.  Picked per
-// (m, s, arithmetic) by the autotuner below; all give identical results.
+// with NS stages and the shared memory of one or two CTAs per SM.  7:
+// k_matvec_b (compile-time block size; double-float, s = 2..4, m = 12, 20,
+// 24, 40 or 50).  8: k_matvec_rb (the same, register-blocked: four rows per
+// thread, two for m = 50).  Picked per (m, s, arithmetic) by the autotuner below; all
+// give identical results; a variant that does not apply runs variant 0.
 struct MvVariant {
-    int ch, threads;  // k_matvec
+    int ch, threads;  // k_matvec / k_matvec_b
     int ns, per_sm;   // k_matvec_pipe (ns > 0)
+    int fixed;        // 1: k_matvec_b, 2: k_matvec_rb
 };
-const MvVariant kMvVariants[] = {{8, 256, 0, 0}, {4, 256, 0, 0}, {2, 256, 0, 0}, {4, 128, 0, 0},
-                                 {0, 0, 2, 1},   {0, 0, 3, 1},   {0, 0, 2, 2}};
-const int kNumMvVariants = 7;
+const MvVariant kMvVariants[] = {{8, 256, 0, 0, 0}, {4, 256, 0, 0, 0}, {2, 256, 0, 0, 0}, {4, 128, 0, 0, 0},
+                                 {0, 0, 2, 1, 0},   {0, 0, 3, 1, 0},   {0, 0, 2, 2, 0},   {4, 256, 0, 0, 1},
+                                 {2, 256, 0, 0, 2}};
+const int kNumMvVariants = 9;
 
 struct DevLimits {
     int sms = 0, optin = 0, per_sm = 0;
@@ -487,9 +612,44 @@ void run_matvec_pipe(const MatvecParams &P, int G, int ns, int *err, cudaStream_
     k_matvec_pipe<AR, S><<<(int)grid, threads, smem, st>>>(P, G, ns, err);
 }
 
+template <int S, int B>
+bool run_matvec_b(const MatvecParams &P, cudaStream_t st) {
+    if (P.m != B) return false;
+    constexpr int G = 256 / B;
+    const long long g = (P.T + G - 1) / G;
+    k_matvec_b<S, B, 4><<<(int)g, (G * B + 31) / 32 * 32, 0, st>>>(P);
+    return true;
+}
+
+template <int S, int B, int H>
+bool run_matvec_rb(const MatvecParams &P, cudaStream_t st) {
+    if (P.m != B) return false;
+    constexpr int GT = B / (2 * H), G = 256 / GT;
+    const long long g = (P.T + G - 1) / G;
+    k_matvec_rb<S, B, H, 2><<<(int)g, (G * GT + 31) / 32 * 32, 0, st>>>(P);
+    return true;
+}
+
+template <class AR, int S>
+bool run_matvec_fixed(const MatvecParams &P, int form, cudaStream_t st) {
+    if constexpr (std::is_same<AR, ArDF>::value && S >= 2 && S <= 4) {
+        if ((((uintptr_t)P.x | (uintptr_t)P.J | (uintptr_t)P.M) & 15) != 0) return false;
+        if (form == 2)
+            return run_matvec_rb<S, 40, 2>(P, st) || run_matvec_rb<S, 50, 1>(P, st) ||
+                   run_matvec_rb<S, 24, 2>(P, st) || run_matvec_rb<S, 20, 2>(P, st) || run_matvec_rb<S, 12, 2>(P, st);
+        return run_matvec_b<S, 40>(P, st) || run_matvec_b<S, 50>(P, st) || run_matvec_b<S, 24>(P, st) ||
+               run_matvec_b<S, 20>(P, st) || run_matvec_b<S, 12>(P, st);
+    }
+    return false;
+}
+
 template <class AR, int S>
 void run_matvec(const MatvecParams &P, int variant, int *err, cudaStream_t st) {
     const MvVariant v = kMvVariants[variant];
+    if (v.fixed) {
+        if (!run_matvec_fixed<AR, S>(P, v.fixed, st)) run_matvec_ch<AR, S, 8>(P, 256, st);
+        return;
+    }
     if (v.ns > 0) {
         const int G = pipe_groups(P, S, v);
         if (G > 0) {
@@ -529,7 +689,7 @@ std::mutex g_tune_mu;
 std::map<long long, int> g_tune;
 
 int tune_key_variant(irk_ctx *c, const MatvecParams &P) {
-    // IRK_MATVEC_VARIANT=<0..6> pins the variant (tests compare them)
+    // IRK_MATVEC_VARIANT=<0..8> pins the variant (tests compare them)
     if (const char *pin = getenv("IRK_MATVEC_VARIANT")) {
         const int v = atoi(pin);
         if (v >= 0 && v < kNumMvVariants) return v;

@@ -152,7 +152,7 @@ class Solver:
             opt.shift = self._shift.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         if stream is not None:
             opt.stream = ctypes.c_void_p(int(stream))
-        opt.timing = 1 if timing else 0
+        opt.timing = int(timing) if timing in (0, 1, 2) else (1 if timing else 0)
         opt.sweep = {"auto": 0, "levels": 1}[sweep]
         opt.ordering = {"natural": 0, "multicolor": 1}[ordering]
         opt.partitions = int(partitions)

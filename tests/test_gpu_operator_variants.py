@@ -1,8 +1,10 @@
 """Launch variants of the operator product (Sec. 4.1) through the C ABI.
 
 The autotuner picks one of several launches of the same product: the
-register-streaming kernel with different chunk widths and CTA sizes, and the
-bulk-copy pipelined kernel with 2 or 3 shared-memory stages.  All of them
+register-streaming kernel with different chunk widths and CTA sizes, the
+bulk-copy pipelined kernel with 2 or 3 shared-memory stages, and the
+register-streaming kernel with the block size fixed at compile time, one or
+four rows per thread.  All of them
 accumulate every output in the same order, so each one, pinned with
 IRK_MATVEC_VARIANT, must give a result bitwise equal to variant 0's, and that
 result must match the FP64 oracle (1e-13 relative, the operator bar).
@@ -19,7 +21,7 @@ from paper_1701_07181_gb300 import inputs
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-N_VARIANTS = 7
+N_VARIANTS = 9
 
 
 def dev(a):
@@ -57,7 +59,7 @@ def test_operator_variants_bitwise_equal(monkeypatch, krylov, kind, s, m):
     assert rel(outs[0], y_ref) <= 1e-13
 
 
-@pytest.mark.parametrize("variant", [4, 5, 6])
+@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8])
 def test_solve_with_pipelined_product_is_bitwise_equal(monkeypatch, variant):
     """The residual form (y = rhs - B x) of the pipelined kernel, inside a
     full preconditioned solve: same W and iteration count as variant 0."""
