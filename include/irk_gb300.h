@@ -355,8 +355,9 @@ typedef struct {
      * not fit or m is odd it runs variant 0's launch), 7 register-streaming
      * kernel with the block size fixed at compile time (double-float Krylov,
      * s = 2..4, m = 12, 20, 24, 40 or 50; else variant 0's launch), 8 the
-     * same register-blocked (four rows per thread, two for m = 50); -1 before
-     * the first product.  The environment variable IRK_MATVEC_VARIANT=<0..8>, read when
+     * same register-blocked (four rows per thread, two for m = 50), 9 as 7
+     * with eight columns of loads in flight per thread; -1 before the first
+     * product.  The environment variable IRK_MATVEC_VARIANT=<0..9>, read when
      * a context makes its first product, pins the variant.  Every variant
      * gives the same result bit for bit. */
     int matvec_variant;
@@ -381,6 +382,12 @@ typedef struct {
     int sweep_two_colour;
 } irk_stats;
 IRK_API int irk_get_stats(const irk_ctx *ctx, irk_stats *out);
+
+/* Change irk_options.timing of a live context (0, 1 or 2) for the calls that
+ * follow, e.g. to time a sample of a long run.  Leaving timing = 2 keeps the
+ * marks already recorded: the next irk_get_stats made with timing = 2 still
+ * reports them.  IRK_ERR_INVALID for another value or a NULL context. */
+IRK_API int irk_set_timing(irk_ctx *ctx, int timing);
 
 /* Release every resource of the context (NULL is allowed). */
 IRK_API void irk_destroy(irk_ctx *ctx);

@@ -716,6 +716,19 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     return rc;
 }
 
+int irk_set_timing(irk_ctx *c, int timing) {
+    if (!c || timing < 0 || timing > 2) return IRK_ERR_INVALID;
+    if (c->opt.timing == 2 && timing != 2) {
+        // keep what was recorded in the running totals (read at the next
+        // irk_get_stats under timing = 2)
+        cudaStreamSynchronize(c->stream);
+        tflush(c);
+    }
+    if (c->opt.timing == 1 && timing != 1) c->tused = 0;
+    c->opt.timing = timing;
+    return IRK_OK;
+}
+
 int irk_get_stats(const irk_ctx *cc, irk_stats *out) {
     if (!cc || !out) return IRK_ERR_INVALID;
     if (cc->opt.timing == 2) {

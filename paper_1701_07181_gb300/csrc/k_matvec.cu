@@ -547,18 +547,19 @@ int grid_for(long long work, int threads) {
 // loads are in flight per thread) x threads per CTA.  4-6: k_matvec_pipe
 // with NS stages and the shared memory of one or two CTAs per SM.  7:
 // k_matvec_b (compile-time block size; double-float, s = 2..4, m = 12, 20,
-// 24, 40 or 50).  8: k_matvec_rb (the same, register-blocked: four rows per
-// thread, two for m = 50).  Picked per (m, s, arithmetic) by the autotuner below; all
+// 24, 40 or 50; four columns of loads in flight).  8: k_matvec_rb (the
+// same, register-blocked: four rows per thread, two for m = 50).  9:
+// k_matvec_b with eight columns in flight.  Picked per (m, s, arithmetic) by the autotuner below; all
 // give identical results; a variant that does not apply runs variant 0.
 struct MvVariant {
     int ch, threads;  // k_matvec / k_matvec_b
     int ns, per_sm;   // k_matvec_pipe (ns > 0)
-    int fixed;        // 1: k_matvec_b, 2: k_matvec_rb
+    int fixed;        // 1: k_matvec_b, 2: k_matvec_rb, 3: k_matvec_b with CH = 8
 };
 const MvVariant kMvVariants[] = {{8, 256, 0, 0, 0}, {4, 256, 0, 0, 0}, {2, 256, 0, 0, 0}, {4, 128, 0, 0, 0},
                                  {0, 0, 2, 1, 0},   {0, 0, 3, 1, 0},   {0, 0, 2, 2, 0},   {4, 256, 0, 0, 1},
-                                 {2, 256, 0, 0, 2}};
-const int kNumMvVariants = 9;
+                                 {2, 256, 0, 0, 2}, {8, 256, 0, 0, 3}};
+const int kNumMvVariants = 10;
 
 struct DevLimits {
     int sms = 0, optin = 0, per_sm = 0;
@@ -612,12 +613,15 @@ void run_matvec_pipe(const MatvecParams &P, int G, int ns, int *err, cudaStream_
     k_matvec_pipe<AR, S><<<(int)grid, threads, smem, st>>>(P, G, ns, err);
 }
 
-template <int S, int B>
+// k_matvec_b, one element row per group (a grid capped at the resident CTAs,
+// striding over rows, measured slower: 0.316 -> 0.323 ms and 1.23 -> 1.33 ms
+// on the two workloads), CH columns of loads in flight per thread.
+template <int S, int B, int CH>
 bool run_matvec_b(const MatvecParams &P, cudaStream_t st) {
     if (P.m != B) return false;
     constexpr int G = 256 / B;
     const long long g = (P.T + G - 1) / G;
-    k_matvec_b<S, B, 4><<<(int)g, (G * B + 31) / 32 * 32, 0, st>>>(P);
+    k_matvec_b<S, B, CH><<<(int)g, (G * B + 31) / 32 * 32, 0, st>>>(P);
     return true;
 }
 
@@ -637,8 +641,11 @@ bool run_matvec_fixed(const MatvecParams &P, int form, cudaStream_t st) {
         if (form == 2)
             return run_matvec_rb<S, 40, 2>(P, st) || run_matvec_rb<S, 50, 1>(P, st) ||
                    run_matvec_rb<S, 24, 2>(P, st) || run_matvec_rb<S, 20, 2>(P, st) || run_matvec_rb<S, 12, 2>(P, st);
-        return run_matvec_b<S, 40>(P, st) || run_matvec_b<S, 50>(P, st) || run_matvec_b<S, 24>(P, st) ||
-               run_matvec_b<S, 20>(P, st) || run_matvec_b<S, 12>(P, st);
+        if (form == 3)
+            return run_matvec_b<S, 40, 8>(P, st) || run_matvec_b<S, 50, 8>(P, st) ||
+                   run_matvec_b<S, 24, 8>(P, st) || run_matvec_b<S, 20, 8>(P, st) || run_matvec_b<S, 12, 8>(P, st);
+        return run_matvec_b<S, 40, 4>(P, st) || run_matvec_b<S, 50, 4>(P, st) || run_matvec_b<S, 24, 4>(P, st) ||
+               run_matvec_b<S, 20, 4>(P, st) || run_matvec_b<S, 12, 4>(P, st);
     }
     return false;
 }
@@ -689,7 +696,7 @@ std::mutex g_tune_mu;
 std::map<long long, int> g_tune;
 
 int tune_key_variant(irk_ctx *c, const MatvecParams &P) {
-    // IRK_MATVEC_VARIANT=<0..8> pins the variant (tests compare them)
+    // IRK_MATVEC_VARIANT=<0..9> pins the variant (tests compare them)
     if (const char *pin = getenv("IRK_MATVEC_VARIANT")) {
         const int v = atoi(pin);
         if (v >= 0 && v < kNumMvVariants) return v;

@@ -60,7 +60,7 @@ EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor"
            "irk_apply_operator", "irk_apply_precond", "irk_get_stats", "irk_destroy",
            "irk_strerror", "irk_apply_precond_noalloc", "irk_group_create", "irk_group_submit",
            "irk_group_step", "irk_group_query", "irk_group_collect", "irk_group_device_bytes",
-           "irk_group_destroy", "irk_dirk_setup", "irk_dirk_step", "irk_dirk_destroy"]
+           "irk_group_destroy", "irk_dirk_setup", "irk_dirk_step", "irk_dirk_destroy", "irk_set_timing"]
 
 
 def load():
@@ -83,6 +83,7 @@ def load():
         lib.irk_apply_operator.argtypes = [P, P, P, D, I]
         lib.irk_apply_precond.argtypes = [P, P, P, I]
         lib.irk_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
+        lib.irk_set_timing.argtypes = [P, I]
         lib.irk_destroy.argtypes = [P]
         lib.irk_destroy.restype = None
         lib.irk_strerror.argtypes = [I]
@@ -225,6 +226,10 @@ class Solver:
         Zp, keepz, _ = _ptr(Z, np.float64)
         self._check(self._lib.irk_apply_precond(self._h, Vp, Zp, sp), "irk_apply_precond")
         return Z
+
+    def set_timing(self, timing):
+        """irk_set_timing: 0, 1 or 2 (see irk_options.timing) for the calls that follow."""
+        self._check(self._lib.irk_set_timing(self._h, int(timing)), "irk_set_timing")
 
     def stats(self):
         st = Stats()

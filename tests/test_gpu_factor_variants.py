@@ -125,3 +125,4 @@ def test_coupled_preconditioner_keeps_per_entry_kernel(monkeypatch):
         assert S.stats()["factor_fused_levels"] == 0
         W, it, rr, rc = S.solve(P.R, 0.3, rtol=1e-8)
     assert rc == 0 and rr <= 1e-8
+

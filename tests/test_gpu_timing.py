@@ -48,3 +48,28 @@ def test_deferred_timing_totals_match_per_solve_timing(monkeypatch):
         assert again[k] == 0.0, k
     assert tot["matvec_ms"] > 0.0 and tot["precond_ms"] > 0.0 and tot["ortho_ms"] > 0.0
     assert again["n_matvec"] == 0 and again["kernel_launches"] == 0
+
+
+def test_set_timing_samples_calls(monkeypatch):
+    """irk_set_timing switches the events on and off between calls: marks
+    recorded under timing = 2 survive a switch to 0 and are reported by the
+    next irk_get_stats under timing = 2; calls made with timing 0 add none."""
+    from paper_1701_07181_gb300 import irk
+    monkeypatch.setenv("IRK_MATVEC_VARIANT", "0")
+    P = inputs.make_problem(inputs.mesh_2d_periodic(12, 10), 20, 3, 0.2, 4.0, seed=4)
+    with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec="fp32", krylov="df64",
+                    ordering="multicolor", timing=1) as S:
+        S.solve(P.R, 0.05, rtol=1e-8)
+        one = S.stats()
+    with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec="fp32", krylov="df64",
+                    ordering="multicolor", timing=2) as S:
+        S.stats()
+        S.solve(P.R, 0.05, rtol=1e-8)   # timed
+        S.set_timing(0)
+        S.solve(P.R, 0.2, rtol=1e-8)    # not timed
+        S.set_timing(2)
+        tot = S.stats()
+        with pytest.raises(irk.IrkError):
+            S.set_timing(3)
+    assert tot["n_matvec"] == one["n_matvec"] and tot["n_ortho"] == one["n_ortho"]
+    assert tot["matvec_ms"] > 0.0
