@@ -44,7 +44,7 @@ TIME_EVERY = 4  # per-kernel CUDA events on every 4th timed step
 WORKLOAD = ("2D periodic 100x100 split grid, T=20000 triangles, r=3, p=3 (m=40), Radau IIA s=3, "
             "dt in {0.01,0.1,1}, FGMRES(30) rtol 1e-8, shifted uncoupled block ILU(0)")
 SOLVER = ("double-float Krylov, FP32 factors, shifted uncoupled block ILU(0) in two-colour order "
-          "(all stages per launch, persistent sweeps)")
+          "(all stages per launch; the preconditioner in two launches)")
 
 
 def algorithmic_bytes(T, m, r, s):
