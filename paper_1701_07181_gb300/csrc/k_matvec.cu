@@ -166,6 +166,63 @@ __device__ __forceinline__ void accum_block_b(df_acc (&dst)[S], const vec8 *Bp, 
     }
 }
 
+// accum_block_b with the block loads one chunk ahead: chunk c + CH's
+// columns are requested before chunk c's arithmetic, so the loads overlap a
+// chunk of work instead of stalling right before it.  Same operation order.
+// (Reaching across into the next block's first chunk as well costs
+// registers, hence occupancy, and measured slower: 0.30 -> 0.35 ms.)
+template <int S, int B, int CH>
+__device__ __forceinline__ void accum_block_sp(df_acc (&dst)[S], const vec8 *Bp, const vec8 *x) {
+    df64 cur[CH], nxt[CH];
+#pragma unroll
+    for (int u = 0; u < CH; ++u)
+        if (u < B) cur[u] = ArDF::ld(Bp + u * B);
+#pragma unroll
+    for (int c0 = 0; c0 < B; c0 += CH) {
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (c0 + CH + u < B) nxt[u] = ArDF::ld(Bp + (c0 + CH + u) * B);
+        df64 xv[S][CH];
+#pragma unroll
+        for (int l = 0; l < S; ++l)
+#pragma unroll
+            for (int u = 0; u < CH; u += 2)
+                if (c0 + u < B) {
+                    const float4 f = __ldg(reinterpret_cast<const float4 *>(x + l * B + c0 + u));
+                    xv[l][u] = df_make(f.x, f.y);
+                    xv[l][u + 1] = df_make(f.z, f.w);
+                }
+#pragma unroll
+        for (int u = 0; u < CH; ++u)
+            if (c0 + u < B)
+#pragma unroll
+                for (int l = 0; l < S; ++l) ArDF::fma(dst[l], cur[u], xv[l][u]);
+#pragma unroll
+        for (int u = 0; u < CH; ++u) cur[u] = nxt[u];
+    }
+}
+
+template <int S, int B, int CH>
+__global__ void __launch_bounds__(256) k_matvec_sp(MatvecParams P) {
+    constexpr int G = 256 / B;
+    constexpr long long BB = (long long)B * B, SB = (long long)S * B;
+    const int g = threadIdx.x / B;
+    const int a = threadIdx.x - g * B;
+    if (g >= G) return;
+    for (long long i = (long long)blockIdx.x * G + g; i < P.T; i += (long long)gridDim.x * G) {
+        df_acc t[S], z[S];
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+            t[l] = ArDF::zero();
+            z[l] = ArDF::zero();
+        }
+        const int p0 = P.rp[i], p1 = P.rp[i + 1];
+        for (int p = p0; p < p1; ++p) accum_block_sp<S, B, CH>(t, P.J + p * BB + a, P.x + P.ci[p] * SB);
+        if (P.form != IRK_FORM_JACOBIAN) accum_block_sp<S, B, CH>(z, P.M + i * BB + a, P.x + i * SB);
+        store_row<ArDF, S>(P, i, a, t, z);
+    }
+}
+
 template <int S, int B, int CH>
 __global__ void __launch_bounds__(256) k_matvec_b(MatvecParams P) {
     constexpr int G = 256 / B;
@@ -549,17 +606,18 @@ int grid_for(long long work, int threads) {
 // k_matvec_b (compile-time block size; double-float, s = 2..4, m = 12, 20,
 // 24, 40 or 50; four columns of loads in flight).  8: k_matvec_rb (the
 // same, register-blocked: four rows per thread, two for m = 50).  9:
-// k_matvec_b with eight columns in flight.  Picked per (m, s, arithmetic) by the autotuner below; all
+// k_matvec_b with eight columns in flight.  10: k_matvec_sp (k_matvec_b with
+// the block loads one chunk ahead).  Picked per (m, s, arithmetic) by the autotuner below; all
 // give identical results; a variant that does not apply runs variant 0.
 struct MvVariant {
     int ch, threads;  // k_matvec / k_matvec_b
     int ns, per_sm;   // k_matvec_pipe (ns > 0)
-    int fixed;        // 1: k_matvec_b, 2: k_matvec_rb, 3: k_matvec_b with CH = 8
+    int fixed;        // 1: k_matvec_b, 2: k_matvec_rb, 3: k_matvec_b with CH = 8, 4: k_matvec_sp
 };
 const MvVariant kMvVariants[] = {{8, 256, 0, 0, 0}, {4, 256, 0, 0, 0}, {2, 256, 0, 0, 0}, {4, 128, 0, 0, 0},
                                  {0, 0, 2, 1, 0},   {0, 0, 3, 1, 0},   {0, 0, 2, 2, 0},   {4, 256, 0, 0, 1},
-                                 {2, 256, 0, 0, 2}, {8, 256, 0, 0, 3}};
-const int kNumMvVariants = 10;
+                                 {2, 256, 0, 0, 2}, {8, 256, 0, 0, 3}, {4, 256, 0, 0, 4}};
+const int kNumMvVariants = 11;
 
 struct DevLimits {
     int sms = 0, optin = 0, per_sm = 0;
@@ -634,6 +692,15 @@ bool run_matvec_rb(const MatvecParams &P, cudaStream_t st) {
     return true;
 }
 
+template <int S, int B>
+bool run_matvec_sp(const MatvecParams &P, cudaStream_t st) {
+    if (P.m != B) return false;
+    constexpr int G = 256 / B;
+    const long long g = (P.T + G - 1) / G;
+    k_matvec_sp<S, B, 4><<<(int)g, (G * B + 31) / 32 * 32, 0, st>>>(P);
+    return true;
+}
+
 template <class AR, int S>
 bool run_matvec_fixed(const MatvecParams &P, int form, cudaStream_t st) {
     if constexpr (std::is_same<AR, ArDF>::value && S >= 2 && S <= 4) {
@@ -641,6 +708,9 @@ bool run_matvec_fixed(const MatvecParams &P, int form, cudaStream_t st) {
         if (form == 2)
             return run_matvec_rb<S, 40, 2>(P, st) || run_matvec_rb<S, 50, 1>(P, st) ||
                    run_matvec_rb<S, 24, 2>(P, st) || run_matvec_rb<S, 20, 2>(P, st) || run_matvec_rb<S, 12, 2>(P, st);
+        if (form == 4)
+            return run_matvec_sp<S, 40>(P, st) || run_matvec_sp<S, 50>(P, st) || run_matvec_sp<S, 24>(P, st) ||
+                   run_matvec_sp<S, 20>(P, st) || run_matvec_sp<S, 12>(P, st);
         if (form == 3)
             return run_matvec_b<S, 40, 8>(P, st) || run_matvec_b<S, 50, 8>(P, st) ||
                    run_matvec_b<S, 24, 8>(P, st) || run_matvec_b<S, 20, 8>(P, st) || run_matvec_b<S, 12, 8>(P, st);
@@ -696,7 +766,7 @@ std::mutex g_tune_mu;
 std::map<long long, int> g_tune;
 
 int tune_key_variant(irk_ctx *c, const MatvecParams &P) {
-    // IRK_MATVEC_VARIANT=<0..9> pins the variant (tests compare them)
+    // IRK_MATVEC_VARIANT=<0..10> pins the variant (tests compare them)
     if (const char *pin = getenv("IRK_MATVEC_VARIANT")) {
         const int v = atoi(pin);
         if (v >= 0 && v < kNumMvVariants) return v;

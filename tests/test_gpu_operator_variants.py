@@ -21,7 +21,7 @@ from paper_1701_07181_gb300 import inputs
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-N_VARIANTS = 10
+N_VARIANTS = 11
 
 
 def dev(a):
@@ -59,7 +59,7 @@ def test_operator_variants_bitwise_equal(monkeypatch, krylov, kind, s, m):
     assert rel(outs[0], y_ref) <= 1e-13
 
 
-@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8, 9, 10])
 def test_solve_with_pipelined_product_is_bitwise_equal(monkeypatch, variant):
     """The residual form (y = rhs - B x) of the pipelined kernel, inside a
     full preconditioned solve: same W and iteration count as variant 0."""
