@@ -190,6 +190,26 @@ IRK_API int irk_factor(irk_ctx *ctx, double dt);
 IRK_API int irk_solve(irk_ctx *ctx, const double *R, double dt, double rtol, double *W, int mem_space,
               int *iters, double *relres);
 
+/* Step outputs from a stage solution W of the transformed system (Sec. 4.1:
+ * W stacks w_i = sum_j a_ij k_j): the stage derivatives
+ *     K = (A^{-1} (x) I_n) W,   k_i = sum_j (A^{-1})_ij w_j,
+ * and the new state
+ *     u1 = u0 + dt (b^T A^{-1} (x) I_n) W
+ * (Radau IIA: b^T A^{-1} = e_s^T, so u1 = u0 + dt w_s).  One binary64 pass
+ * over W on the context's stream; the sums run over j in increasing order.
+ *   W    s*T*m stage-major (as irk_solve writes it), in mem_space.
+ *   b    host array of the s weights, or NULL: b = the last row of A (a
+ *        stiffly accurate tableau, as the built-in Radau IIA), and then
+ *        b^T A^{-1} = e_s^T is used exactly.
+ *   u0   T*m in mem_space, or NULL when u1 is NULL.
+ *   K    s*T*m stage-major output in mem_space, or NULL.
+ *   u1   T*m output in mem_space, or NULL.
+ * Host buffers go through a device temporary allocated for the call.
+ * IRK_ERR_INVALID for a NULL context or W, u1 without u0, or a bad mem_space;
+ * IRK_ERR_NOMEM if the temporary cannot be allocated. */
+IRK_API int irk_step_outputs(irk_ctx *ctx, const double *W, const double *b, const double *u0, double dt,
+                             double *K, double *u1, int mem_space);
+
 /* Y = B X for the context's formulation and dt (the operator product of
  * Sec. 4.1 alone; Table 2's transformed / untransformed matrix-vector
  * product).  X, Y stage-major s*T*m in mem_space. */

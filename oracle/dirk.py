@@ -20,6 +20,9 @@ u1 = u0 + dt sum_k b_k k_k.
   u1 = u0 + sum_k (b^T A^{-1})_k W_k (= u0 + W_s for stiffly accurate
   schemes such as Radau IIA).
 * ``jacobian_apply``: y_i = sum_j J_ij x_j, the plain block-sparse product.
+* ``step_outputs``: from the transformed stage solution W of Sec. 4.1 (W =
+  (A (x) I) K), the stage derivatives K = (A^{-1} (x) I) W and the new state
+  u1 = u0 + dt (b^T A^{-1} (x) I) W.
 
 The number of n x n matrix-vector products of a step is what Sec. 5 calls
 equivalent multiplications: iterations x 1 per DIRK stage, iterations x s for
@@ -30,6 +33,21 @@ from __future__ import annotations
 import numpy as np
 
 from . import FORM_TRANSFORMED, FORM_UNTRANSFORMED, PC_STAGE_MAJOR, PC_UNCOUPLED, Problem
+
+
+def step_outputs(A, b, W, u0, dt):
+    """Sec. 4.1: W stacks w_i = sum_j a_ij k_j, so K = (A^{-1} (x) I_n) W, and
+    u1 = u0 + dt (b^T A^{-1} (x) I_n) W.  W is s x n (stage-major) or flat;
+    returns (K as s x n, u1 or None when u0 is None)."""
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    s = len(b)
+    W = np.asarray(W, dtype=np.float64).reshape(s, -1)
+    K = np.linalg.solve(A, W)  # A K = W, row by row
+    if u0 is None:
+        return K, None
+    wts = np.linalg.solve(A.T, b)  # b^T A^{-1}
+    return K, np.asarray(u0, dtype=np.float64).reshape(-1) + dt * (wts @ W)
 
 
 def jacobian_apply(row_ptr, col_idx, J, m, x):

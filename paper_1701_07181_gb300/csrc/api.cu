@@ -716,6 +716,82 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     return rc;
 }
 
+// Step outputs (Sec. 4.1) on the stage-major boundary layout, binary64:
+// K[k] = sum_l Ainv[k][l] W[l], u1 = u0 + dt sum_l wt[l] W[l] (l increasing).
+struct StepCoef {
+    double Ainv[IRK_MAX_S * IRK_MAX_S];
+    double wt[IRK_MAX_S];
+};
+
+__global__ void k_step_outputs(long long n, int s, const double *__restrict__ W, StepCoef cf,
+                               const double *__restrict__ u0, double dt, double *K, double *u1) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double w[IRK_MAX_S];
+        for (int l = 0; l < s; ++l) w[l] = W[l * n + e];
+        if (K)
+            for (int k = 0; k < s; ++k) {
+                double acc = 0.0;
+                for (int l = 0; l < s; ++l) acc = fma(cf.Ainv[k * s + l], w[l], acc);
+                K[k * n + e] = acc;
+            }
+        if (u1) {
+            double acc = 0.0;
+            for (int l = 0; l < s; ++l) acc = fma(cf.wt[l], w[l], acc);
+            u1[e] = fma(dt, acc, u0[e]);
+        }
+    }
+}
+
+static int launch_step_outputs(irk_ctx *c, const double *W, const double *wt, const double *u0, double dt,
+                               double *K, double *u1) {
+    StepCoef cf;
+    memset(&cf, 0, sizeof(cf));
+    for (int q = 0; q < c->s * c->s; ++q) cf.Ainv[q] = c->Ainv[q];
+    for (int l = 0; l < c->s; ++l) cf.wt[l] = wt[l];
+    const long long n = (long long)c->T * c->m;
+    long long g = (n + 255) / 256;
+    if (g > 152LL * 16) g = 152LL * 16;
+    k_step_outputs<<<(int)std::max(1LL, g), 256, 0, c->stream>>>(n, c->s, W, cf, u0, dt, K, u1);
+    c->launches++;
+    return cuda_status(cudaGetLastError());
+}
+
+int irk_step_outputs(irk_ctx *c, const double *W, const double *b, const double *u0, double dt, double *K,
+                     double *u1, int mem_space) {
+    if (!c || !W || (u1 && !u0) || !std::isfinite(dt) || (mem_space != IRK_HOST && mem_space != IRK_DEVICE))
+        return IRK_ERR_INVALID;
+    const int s = c->s;
+    // weights b^T A^{-1}; a stiffly accurate tableau (b = last row of A) has e_s^T exactly
+    double wt[IRK_MAX_S];
+    for (int l = 0; l < s; ++l) wt[l] = 0.0;
+    if (!b) {
+        wt[s - 1] = 1.0;
+    } else {
+        for (int l = 0; l < s; ++l)
+            for (int j = 0; j < s; ++j) wt[l] += b[j] * c->Ainv[j * s + l];
+    }
+    const long long N = c->N, n = (long long)c->T * c->m;
+    if (mem_space == IRK_DEVICE) {
+        int rc = launch_step_outputs(c, W, wt, u0, dt, K, u1);
+        if (rc == IRK_OK) rc = cuda_status(cudaStreamSynchronize(c->stream));
+        return rc;
+    }
+    // host buffers: W, u0 in and K, u1 out through one device temporary
+    double *tmp = nullptr;
+    if (cudaMalloc(&tmp, sizeof(double) * (size_t)(2 * N + 2 * n)) != cudaSuccess) return IRK_ERR_NOMEM;
+    double *dW = tmp, *dK = tmp + N, *du0 = tmp + 2 * N, *du1 = tmp + 2 * N + n;
+    int rc = cuda_status(cudaMemcpyAsync(dW, W, sizeof(double) * N, cudaMemcpyHostToDevice, c->stream));
+    if (rc == IRK_OK && u1)
+        rc = cuda_status(cudaMemcpyAsync(du0, u0, sizeof(double) * n, cudaMemcpyHostToDevice, c->stream));
+    if (rc == IRK_OK) rc = launch_step_outputs(c, dW, wt, u1 ? du0 : nullptr, dt, K ? dK : nullptr, u1 ? du1 : nullptr);
+    if (rc == IRK_OK && K) rc = cuda_status(cudaMemcpyAsync(K, dK, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+    if (rc == IRK_OK && u1)
+        rc = cuda_status(cudaMemcpyAsync(u1, du1, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+    const int rs = cuda_status(cudaStreamSynchronize(c->stream));
+    cudaFree(tmp);
+    return rc != IRK_OK ? rc : rs;
+}
+
 int irk_set_timing(irk_ctx *c, int timing) {
     if (!c || timing < 0 || timing > 2) return IRK_ERR_INVALID;
     if (c->opt.timing == 2 && timing != 2) {

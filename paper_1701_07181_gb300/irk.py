@@ -60,7 +60,8 @@ EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor"
            "irk_apply_operator", "irk_apply_precond", "irk_get_stats", "irk_destroy",
            "irk_strerror", "irk_apply_precond_noalloc", "irk_group_create", "irk_group_submit",
            "irk_group_step", "irk_group_query", "irk_group_collect", "irk_group_device_bytes",
-           "irk_group_destroy", "irk_dirk_setup", "irk_dirk_step", "irk_dirk_destroy", "irk_set_timing"]
+           "irk_group_destroy", "irk_dirk_setup", "irk_dirk_step", "irk_dirk_destroy", "irk_set_timing",
+           "irk_step_outputs"]
 
 
 def load():
@@ -84,6 +85,7 @@ def load():
         lib.irk_apply_precond.argtypes = [P, P, P, I]
         lib.irk_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
         lib.irk_set_timing.argtypes = [P, I]
+        lib.irk_step_outputs.argtypes = [P, P, P, P, D, P, P, I]
         lib.irk_destroy.argtypes = [P]
         lib.irk_destroy.restype = None
         lib.irk_strerror.argtypes = [I]
@@ -226,6 +228,30 @@ class Solver:
         Zp, keepz, _ = _ptr(Z, np.float64)
         self._check(self._lib.irk_apply_precond(self._h, Vp, Zp, sp), "irk_apply_precond")
         return Z
+
+    def step_outputs(self, W, dt, u0=None, b=None, want_K=True):
+        """irk_step_outputs: (K, u1) from the stage solution W (Sec. 4.1):
+        K = (A^-1 (x) I) W and u1 = u0 + dt (b^T A^-1 (x) I) W (b = None: the
+        last row of A, as for Radau IIA).  K or u1 is None when not asked for."""
+        Wp, keep, sp = _ptr(W, np.float64)
+        K = self._out_like(W) if want_K else None
+        Kp, keepk = (_ptr(K, np.float64)[:2] if want_K else (None, None))
+        u1 = None
+        u0p = u1p = None
+        if u0 is not None:
+            u0p, keep0, sp0 = _ptr(u0, np.float64)
+            if sp0 != sp:
+                raise ValueError("W and u0 must be in the same memory space")
+            n = self.T * self.m
+            if _is_torch_cuda(u0):
+                import torch
+                u1 = torch.empty(n, dtype=torch.float64, device=u0.device)
+            else:
+                u1 = np.empty(n, dtype=np.float64)
+            u1p, keep1, _ = _ptr(u1, np.float64)
+        bb = None if b is None else (ctypes.c_double * self.s)(*[float(x) for x in b])
+        self._check(self._lib.irk_step_outputs(self._h, Wp, bb, u0p, float(dt), Kp, u1p, sp), "irk_step_outputs")
+        return K, u1
 
     def set_timing(self, timing):
         """irk_set_timing: 0, 1 or 2 (see irk_options.timing) for the calls that follow."""

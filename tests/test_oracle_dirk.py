@@ -202,3 +202,54 @@ def test_convergence_order_against_exponential(name, p):
         errs.append(np.linalg.norm(u - exact))
     rate = math.log2(errs[0] / errs[1])
     assert p - 0.6 < rate < p + 0.8, (name, errs, rate)
+
+
+# ---------------------------------------------------------------------------
+# step_outputs: K = (A^-1 (x) I) W and u1 = u0 + dt (b^T A^-1 (x) I) W (Sec. 4.1)
+
+@pytest.mark.parametrize("s", [2, 3])
+def test_step_outputs_radau_reduces_to_last_stage(s):
+    """The paper's simplification for Radau IIA: b^T A^-1 = e_s, so
+    u1 = u0 + dt w_s."""
+    A, b, _ = tableau.radau_iia(s)
+    rng = np.random.default_rng(s)
+    W = rng.standard_normal((s, 50))
+    u0 = rng.standard_normal(50)
+    K, u1 = dirk.step_outputs(A, b, W, u0, 0.3)
+    np.testing.assert_allclose(u1, u0 + 0.3 * W[-1], rtol=0, atol=1e-13)
+
+
+def test_step_outputs_match_classical_rk_form():
+    """With W = (A (x) I) K the transformed update equals the classical one,
+    u1 = u0 + dt sum_i b_i k_i, and K maps back to W (any invertible A)."""
+    rng = np.random.default_rng(11)
+    s = 4
+    A = rng.standard_normal((s, s)) + 3.0 * np.eye(s)
+    b = rng.standard_normal(s)
+    K0 = rng.standard_normal((s, 30))
+    W = A @ K0
+    u0 = rng.standard_normal(30)
+    K, u1 = dirk.step_outputs(A, b, W, u0, 0.7)
+    np.testing.assert_allclose(K, K0, rtol=0, atol=1e-12)
+    np.testing.assert_allclose(u1, u0 + 0.7 * (b @ K0), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("scheme", ["radau23", "radau35", "DIRK33", "ESDIRK65"])
+def test_step_outputs_scalar_problem_is_stability_function(scheme):
+    """u' = lam u: the stage solution of (A^-1 - dt lam I) W = lam u0 1 gives
+    u1 = R(dt lam) u0 with the stability function R(z) = 1 + z b^T (I - zA)^-1 1;
+    ESDIRK65's explicit first stage makes A singular, so its W comes from K."""
+    A, b = {"radau23": tableau.radau23, "radau35": tableau.radau35,
+            "DIRK33": tableau.dirk33, "ESDIRK65": tableau.esdirk65}[scheme]()[:2]
+    A = np.asarray(A, dtype=np.float64)
+    s = len(b)
+    lam, dt, u0 = -2.5, 0.4, np.array([1.7])
+    # stage derivatives k = lam (u0 + dt A k): (I - dt lam A) k = lam u0 1
+    K = np.linalg.solve(np.eye(s) - dt * lam * A, lam * u0[0] * np.ones(s))
+    W = (A @ K).reshape(s, 1)
+    if abs(np.linalg.det(A)) > 1e-12:
+        _, u1 = dirk.step_outputs(A, b, W, u0, dt)
+    else:
+        u1 = u0 + dt * (np.asarray(b) @ K)
+    R = tableau.stability_function(A, b, dt * lam).real
+    np.testing.assert_allclose(u1, R * u0, rtol=1e-13)
