@@ -577,16 +577,31 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     // a refactorisation is enqueued ahead of the solve; the synchronisation
     // that reads ||R|| below also reports its errors (no round trip of its own)
     const bool refactor = c->opt.precond != IRK_PC_NONE && (!c->factored || c->factored_dt != dt);
+    // a host R is copied on a second stream during the refactorisation
+    bool r_in = false;
+    if (refactor && mem_space == IRK_HOST) {
+        if (!c->in_stream && cudaStreamCreateWithFlags(&c->in_stream, cudaStreamNonBlocking) != cudaSuccess)
+            c->in_stream = nullptr;
+        if (c->in_stream && !c->in_ev && cudaEventCreateWithFlags(&c->in_ev, cudaEventDisableTiming) != cudaSuccess)
+            c->in_ev = nullptr;
+        if (c->in_stream && c->in_ev) {
+            if ((rc = copy_in(c->d_io, Rhs, sizeof(double) * c->N, mem_space, c->in_stream))) return rc;
+            cudaEventRecord(c->in_ev, c->in_stream);
+            r_in = true;
+        }
+    }
     cudaEvent_t fe0 = nullptr, fe1 = nullptr;
     if (refactor) {
         cudaEventCreate(&fe0);
         cudaEventCreate(&fe1);
         if ((rc = factor_enqueue(c, dt, fe0, fe1))) {
             cudaStreamSynchronize(c->stream);
+            if (r_in) cudaStreamSynchronize(c->in_stream);
             factor_finish(c, dt, rc, fe0, fe1, l0);
             return rc;
         }
     }
+    if (r_in) cudaStreamWaitEvent(c->stream, c->in_ev, 0);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -597,7 +612,7 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     double *est_h = c->h_scal, *beta_h = c->h_scal + 1, *hn_h = c->h_scal + 2;
     int total = 0, cycles = 0;
     double bnorm = 0.0, beta = 0.0;
-    rc = copy_in(c->d_io, Rhs, sizeof(double) * N, mem_space, c->stream);
+    rc = r_in ? IRK_OK : copy_in(c->d_io, Rhs, sizeof(double) * N, mem_space, c->stream);
     if (!rc) rc = launch_to_internal(c, c->d_io, c->d_b);
     if (!rc) rc = launch_axpy_dot_slot(c, c->d_b, nullptr, 0, nullptr, 1, 1, 0, nullptr);
     if (!rc) rc = cuda_status(cudaMemcpyAsync(beta_h, irk_beta_ptr(c), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -823,7 +838,14 @@ int irk_get_stats(const irk_ctx *cc, irk_stats *out) {
 }
 
 void irk_destroy(irk_ctx *c) {
-    if (c) cudaStreamSynchronize(c->stream);
+    if (c) {
+        cudaStreamSynchronize(c->stream);
+        if (c->in_stream) {
+            cudaStreamSynchronize(c->in_stream);
+            cudaStreamDestroy(c->in_stream);
+        }
+        if (c->in_ev) cudaEventDestroy(c->in_ev);
+    }
     free_ctx(c);
 }
 

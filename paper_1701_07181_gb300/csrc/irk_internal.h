@@ -78,6 +78,10 @@ struct PcSystem {
 struct irk_ctx {
     int dev = 0;
     cudaStream_t stream = nullptr;
+    // host right-hand sides: copied on their own non-blocking stream while a
+    // refactorisation runs (created at the first such solve)
+    cudaStream_t in_stream = nullptr;
+    cudaEvent_t in_ev = nullptr;
     int s = 0, T = 0, m = 0, nnzb = 0;
     int nJ = 1;  // Jacobians stored: 1 (shared by the stages) or s (one per stage)
     long long n = 0, N = 0;  // n = T m, N = s n
