@@ -159,7 +159,10 @@ IRK_API void irk_default_options(irk_options *opt);
  *   s         number of stages, 1 <= s <= 8.
  *   A         host s*s row-major Butcher matrix, invertible; NULL = Radau IIA
  *             with s stages (App. A; computed by collocation).
- *   T, m      elements and block size, T >= 1, 1 <= m <= 128.
+ *   T, m      elements and block size, T >= 1, 1 <= m <= 128; with binary64
+ *             factors m <= 120 (the factorisation keeps two b x b blocks
+ *             and a column in one CTA's 227 KB of shared memory; b = m, or
+ *             s m for IRK_PC_ELEMENT), else IRK_ERR_INVALID.
  *   row_ptr, col_idx, J, M   as in the layout notes above, in mem_space.
  *   opt       NULL = defaults.  The pattern must be structurally symmetric.
  * Copies everything; allocates the Krylov workspace for the given restart.
