@@ -148,7 +148,7 @@ __device__ __forceinline__ void store_pair(double *p, const double (&v)[2]) {
 }
 
 template <class C>
-__global__ void __launch_bounds__(256) k_assemble_stages(long long per_stage, int s, int m, const AsmEntry *ent,
+__global__ void __launch_bounds__(256, 4) k_assemble_stages(long long per_stage, int s, int m, const AsmEntry *ent,
                                                          const vec8 *J, const vec8 *M, int df, AsmTables tab,
                                                          C *vals) {
     const int mm = m * m;
