@@ -10,9 +10,12 @@ stage-uncoupled block ILU(0) with FP32 factors in two-colour element order,
 all stages per launch.
 
 Reported beside it: the plain FP64 GPU path (FP64 factors and Krylov, one
-request at a time), per-phase device times with roofline fractions, the
-end-to-end number through host buffers, and the FP64 oracle on the host
-cores (bounded sample, extrapolated).
+request at a time; in the input order and in the same two-colour order),
+per-phase device times with roofline fractions, the end-to-end number
+through host buffers, every precision variant's iterations, time and error
+against the FP64 oracle, and the FP64 oracle itself on the host cores:
+complete solves, timed, serial (one core) and multi-core (OpenMP build of
+the same source).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 launch with torch.distributed.run: every rank solves its own
@@ -164,107 +167,174 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_sample(P, iters_by_dt):
-    """Oracle (serial C, FP64) on a bounded sample of the workload: the
-    preconditioner build at dt = 0.1 (max_iter 0), and build + 3 FGMRES
-    iterations; solve time per dt = build + iters(dt) * per-iteration time."""
+def arm_config(world):
+    """The workload of a bench line; the same object on both arms."""
+    return {"workload": WORKLOAD, "solver": SOLVER, "solves_per_step": len(DTS),
+            "l2": "inputs larger than L2 (J alone 1.0 GB per rank)", "parallelism": "replicas x%d" % world}
+
+
+def cpu_info():
+    """(model, cores usable by this process) of the host."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                k, _, v = line.partition(":")
+                if k.strip() in ("model name", "Model", "Hardware") and v.strip():
+                    model = v.strip()
+                    break
+    except OSError:
+        pass
+    if model is None:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.startswith("Model name:"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except AttributeError:
+        cores = os.cpu_count()
+    return model or "unknown", cores
+
+
+def oracle_solves(P, dts, omp):
+    """Complete oracle solves (FP64, uncoupled shifted block ILU(0) built for
+    each dt, FGMRES(30) to rtol 1e-8), one per dt, each timed on its own.
+    Returns (seconds per solve, iterations, threads used)."""
     import oracle
-    ref = oracle.Problem(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M)
-    t0 = time.perf_counter()
-    ref.solve(P.R, 0.1, rtol=RTOL, max_iter=0)
-    t_build = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    ref.solve(P.R, 0.1, rtol=RTOL, max_iter=3)
-    t_iter = max(0.0, (time.perf_counter() - t0 - t_build) / 3.0)
-    t_solves = [t_build + iters_by_dt[dt] * t_iter for dt in DTS]
-    return len(DTS) / sum(t_solves), t_build, t_iter
-
-
-def oracle_iters():
-    path = os.path.join(ROOT, "tests", "golden", "oracle_iters_c1.txt")
-    out = {}
-    if os.path.exists(path):
-        for line in open(path):
-            if line.strip() and not line.startswith("#"):
-                f = line.split()
-                out[float(f[0])] = int(f[1])
-    return out
+    threads = oracle.threads() if omp else 1
+    ref = oracle.Problem(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, omp=omp)
+    secs, its = [], []
+    for dt in dts:
+        t0 = time.perf_counter()
+        out = ref.solve(P.R, dt, rtol=RTOL)
+        secs.append(time.perf_counter() - t0)
+        its.append(out["iters"])
+        if out["rc"] != 0 or not out["relres"] <= RTOL:
+            raise RuntimeError("oracle solve did not converge at dt=%g" % dt)
+    return secs, its, threads
 
 
 def run_reference(args):
+    """The oracle on the host cores: every step one complete solve of the
+    full workload (multi-core build), at dt 0.01, 0.1, 1, 0.01, ... in turn."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
     from paper_1701_07181_gb300 import inputs
-    import oracle
     P = inputs.config("c1", seed=0)
-    ref = oracle.Problem(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M)
-    iters = oracle_iters()
-    for _ in range(args.warmup):  # untimed: one operator product
-        ref.apply(P.R, 0.1)
-    times = []
-    for k in range(args.steps):
-        dt = DTS[k % len(DTS)]
-        t0 = time.perf_counter()
-        ref.solve(P.R, dt, rtol=RTOL, max_iter=1)
-        t_step = time.perf_counter() - t0
-        times.append((dt, t_step))
-    # each step: preconditioner build + 1 iteration at its dt; per-iteration
-    # time from the operator product + preconditioner share measured in the
-    # sample below
+    for k in range(args.warmup):
+        oracle_solves(P, [DTS[k % len(DTS)]], omp=True)
     t0 = time.perf_counter()
-    ref.solve(P.R, 0.1, rtol=RTOL, max_iter=0)
-    t_build = time.perf_counter() - t0
-    t_iter = max(0.0, statistics.median([t for _, t in times]) - t_build)
-    est = [t_build + iters.get(dt, 20) * t_iter for dt in DTS]
-    value = len(DTS) / sum(est)
+    its, threads = [], 1
+    for k in range(args.steps):
+        _, it, threads = oracle_solves(P, [DTS[k % len(DTS)]], omp=True)
+        its += it
+    total = time.perf_counter() - t0
+    value = args.steps / total
+    model, cores = cpu_info()
+    sample = ("%d complete oracle solves of the full workload (one per step, dt cycling 0.01/0.1/1), timed "
+              "end to end: multi-core build of the oracle's C source (OpenMP over block rows, the stages' "
+              "factorisations and sweeps, inner products), %d threads on %s" % (args.steps, threads, model))
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 * sum(est) / len(DTS), "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "solver": "oracle: serial C FP64, uncoupled shifted ILU(0)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step: oracle preconditioner build + 1 FGMRES iteration of the "
-                                       "full workload at that step's dt; solve time extrapolated as build + "
-                                       "oracle iteration count (tests/golden/oracle_iters_c1.txt) x "
-                                       "per-iteration time"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": arm_config(world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                             "cpu_model": model, "host_cores": cores},
+            "iters_per_solve": its[: len(DTS)],
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
 
 
-def precision_variants(configs, dev, dt=0.1):
-    """Per workload and factor precision (binary64 / binary32 / bfloat16
-    storage, double-float Krylov; binary64 Krylov for binary64 factors):
-    iterations, time of one factorisation + solve, and the relative
-    difference of W from the binary64 path's W (which the tests pin to the
-    oracle)."""
+def oracle_samples():
+    """Samples of the oracle's W at rtol 1e-12 (tests/golden/oracle_w_c1.txt,
+    written by tests/golden/make_oracle_w_c1.py, which calls only the
+    oracle): {dt: dict(N, norm2, amax, idx, val)}."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_w_c1.txt")
+    out, cur = {}, None
+    if not os.path.exists(path):
+        return out
+    for line in open(path):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        if f[0] == "dt":
+            kv = dict(zip(f[0::2], f[1::2]))
+            cur = {"N": int(kv["N"]), "norm2": float(kv["norm2"]), "amax": float(kv["amax"]), "idx": [],
+                   "val": [], "iters": int(kv["iters"])}
+            out[float(kv["dt"])] = cur
+        else:
+            cur["idx"].append(int(f[0]))
+            cur["val"].append(float(f[1]))
+    for v in out.values():
+        v["idx"] = np.array(v["idx"], dtype=np.int64)
+        v["val"] = np.array(v["val"])
+    return out
+
+
+def sampled_error(W, gold):
+    """Error of W against the oracle on its stored samples: element-wise
+    max_i |W_i - ref_i| / max|ref| (the full vector's maximum) and an
+    estimate of ||W - ref|| / ||ref|| from the samples' mean square."""
+    d = W[gold["idx"]] - gold["val"]
+    return {"max_rel": float(np.max(np.abs(d)) / gold["amax"]),
+            "norm_rel_est": float(np.sqrt(np.mean(d * d) * gold["N"]) / gold["norm2"]),
+            "samples": int(d.size)}
+
+
+def precision_variants(dev):
+    """Per factor precision and Krylov arithmetic, on the benchmark workload
+    (two-colour order, every dt) and on the 48000-tetrahedra workload
+    (dt = 0.1): iterations, time of one factorisation + solve (CUDA events,
+    after a warm-up solve at another dt), and W's error against the FP64
+    oracle solved to 1e-12 (benchmark workload: on the stored oracle samples;
+    tetrahedra: against this run's binary64 GPU path, which the tests pin to
+    the oracle)."""
     import torch
     from paper_1701_07181_gb300 import inputs, irk
+    variants = (("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "df64"), ("bf16", "df64"))
+    gold = oracle_samples()
     out = {}
-    for name in configs:
+    for name, dts in (("c1", DTS), ("c2", (0.1,))):
         P = inputs.config(name, seed=0)
         t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)  # noqa: E731
         rp, ci, J, M, R = t(P.row_ptr), t(P.col_idx), t(P.J), t(P.M), t(P.R)
-        res, ref = {}, None
-        for fprec in ("fp64", "fp32", "bf16"):
-            kry = "fp64" if fprec == "fp64" else "df64"
+        res, ref = {}, {}
+        for fprec, kry in variants:
+            key = "%s_factors_%s_krylov" % (fprec, kry)
+            rows = {}
             with irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec=fprec, krylov=kry,
                             ordering="multicolor") as S:
-                S.solve(R, 2 * dt, rtol=RTOL)  # warm-up (and autotuning)
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record()
-                W, it, rr, rc = S.solve(R, dt, rtol=RTOL)
-                e1.record()
-                torch.cuda.synchronize()
-            Wn = W.cpu().numpy()
-            if ref is None:
-                ref = Wn
-            res[fprec + "_factors"] = {"krylov": kry, "iters": it, "relres": rr, "ms": e0.elapsed_time(e1),
-                                       "rel_diff_from_fp64": float(np.linalg.norm(Wn - ref) / np.linalg.norm(ref))}
-        out[name] = {"T": P.T, "m": P.m, "s": P.s, "dt": dt, **res}
+                for dt in dts:
+                    S.solve(R, 3.7 * dt, rtol=RTOL)  # warm-up (and autotuning); the timed solve refactors
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record()
+                    W, it, rr, rc = S.solve(R, dt, rtol=RTOL)
+                    e1.record()
+                    torch.cuda.synchronize()
+                    Wn = W.cpu().numpy()
+                    row = {"iters": it, "relres": rr, "ms": e0.elapsed_time(e1)}
+                    if name == "c1" and dt in gold:
+                        row["error_vs_oracle"] = sampled_error(Wn, gold[dt])
+                    elif fprec == "fp64":
+                        ref[dt] = Wn
+                    else:
+                        row["rel_diff_from_fp64_gpu"] = float(np.linalg.norm(Wn - ref[dt]) / np.linalg.norm(ref[dt]))
+                    rows[str(dt)] = row
+            ms = sum(r["ms"] for r in rows.values())
+            res[key] = {"per_dt": rows, "solves_per_s": len(dts) / (ms / 1000.0)}
+        out[name] = {"T": P.T, "m": P.m, "s": P.s, "dts": list(dts), **res}
         del rp, ci, J, M, R
+    nsamp = len(gold[DTS[0]]["idx"]) if gold else 0
+    out["note"] = ("c1 errors: on %d stored samples of the oracle's W (tests/golden/oracle_w_c1.txt); the "
+                   "full-vector bars are in tests/test_gpu_fullsize.py" % nsamp)
     return out
 
 
@@ -523,21 +593,27 @@ def main():
     nat_value = world * args.plain_steps * len(DTS) / (nat_ms / 1000.0)
     Sn.close()
 
-    # plain FP64 GPU path, one request at a time
-    Sp = irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec="fp64", krylov="fp64")
-    step(Sp)  # warm-up
-    plain_acc = dict(launches=0, iters=[], matvec_ms=0.0, precond_ms=0.0, ortho_ms=0.0, factor_ms=0.0,
-                     solve_ms=0.0, n_matvec=0, n_precond=0, n_ortho=0)
-    barrier()
-    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    p0.record()
-    for _ in range(args.plain_steps):
-        step(Sp, plain_acc)
-    p1.record()
-    barrier()
-    plain_ms = max_over_ranks(p0.elapsed_time(p1))
-    plain_value = world * args.plain_steps * len(DTS) / (plain_ms / 1000.0)
-    Sp.close()
+    # plain FP64 GPU path, one request at a time: in the input (natural)
+    # element order, and in the benchmark's two-colour order (the speed-up
+    # of precision alone)
+    plain = {}
+    for order in ("natural", "multicolor"):
+        Sp = irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec="fp64", krylov="fp64",
+                        ordering=order)
+        step(Sp)  # warm-up
+        plain_acc = dict(launches=0, iters=[], matvec_ms=0.0, precond_ms=0.0, ortho_ms=0.0, factor_ms=0.0,
+                         solve_ms=0.0, n_matvec=0, n_precond=0, n_ortho=0)
+        barrier()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record()
+        for _ in range(args.plain_steps):
+            step(Sp, plain_acc)
+        p1.record()
+        barrier()
+        plain_ms = max_over_ranks(p0.elapsed_time(p1))
+        plain[order] = (world * args.plain_steps * len(DTS) / (plain_ms / 1000.0), plain_acc["iters"])
+        Sp.close()
+    plain_value = plain["natural"][0]
 
     if rank != 0:
         if dist is not None:
@@ -555,13 +631,13 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "df64 Krylov / f32 factors",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "solver": SOLVER, "solves_per_step": len(DTS),
-                       "l2": "inputs larger than L2 "
-                       "(J alone 1.0 GB per rank)", "parallelism": "replicas x%d" % world,
-                       "iters_per_solve": acc["iters"][: len(DTS)]},
-            "plain_fp64_gpu": {"value": plain_value, "unit": UNIT, "iters_per_solve": plain_acc["iters"],
+            "config": arm_config(world), "iters_per_solve": acc["iters"][: len(DTS)],
+            "plain_fp64_gpu": {"value": plain_value, "unit": UNIT, "iters_per_solve": plain["natural"][1],
                                "solver": "binary64 Krylov and factors, natural order",
-                               "speedup_of_value": value / plain_value},
+                               "speedup_of_value": value / plain_value,
+                               "two_colour_order": {"value": plain["multicolor"][0],
+                                                    "iters_per_solve": plain["multicolor"][1],
+                                                    "speedup_of_value": value / plain["multicolor"][0]}},
             "natural_order_mixed": {"value": nat_value, "unit": UNIT, "iters_per_solve": nat_acc["iters"]},
             "roofline": roofline, "kernels": kernels, "e2e": e2e,
             "gpu_launches": acc["launches"], "clocks": clk,
@@ -569,7 +645,7 @@ def main():
     if not args.no_dirk and world == 1:
         line["dirk_comparison"] = dirk_comparison(P, dev, rp, ci, J, M)
     if not args.no_variants and world == 1:
-        line["precision_variants"] = precision_variants(("c1", "c2"), dev)
+        line["precision_variants"] = precision_variants(dev)
     if not args.no_serving and world == 1 and args.uneven_requests > 0:
         # batched uneven: independent 2D meshes of 500-5000 triangles, p 1..3,
         # s 2..3, all submitted at once (continuous batching of a backlog)
@@ -607,12 +683,24 @@ def main():
         }
         del probs
     if not args.no_cpu_baseline and world == 1:
-        iters = oracle_iters() or {dt: i for dt, i in zip(DTS, plain_acc["iters"])}
-        v, tb, ti = cpu_sample(P, iters)
-        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "oracle (serial C, FP64) preconditioner build (%.1f s) and 3 FGMRES "
-                                          "iterations (%.2f s each) of the full workload at dt=0.1; solves/s "
-                                          "extrapolated with the oracle's iteration counts per dt" % (tb, ti)}
+        # the oracle as it stands, complete solves of the full workload, timed:
+        # serial (one core) at dt = 0.01 (its cheapest solve: a bounded
+        # sample), and the multi-core build at every dt
+        model, host_cores = cpu_info()
+        secs, its, _ = oracle_solves(P, [DTS[0]], omp=False)
+        line["cpu_baseline"] = {"value": 1.0 / secs[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "one complete serial oracle solve (C, FP64) of the full workload at "
+                                          "dt=0.01 (%d iterations, %.1f s), timed end to end on %s"
+                                          % (its[0], secs[0], model),
+                                "cpu_model": model, "host_cores": host_cores}
+        secs, its, threads = oracle_solves(P, DTS, omp=True)
+        line["cpu_baseline_all_cores"] = {
+            "value": len(DTS) / sum(secs), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "complete oracle solves of the full workload at dt 0.01, 0.1, 1 (%s iterations; %s s), "
+                      "multi-core build of the same C source (OpenMP over block rows, the stages' "
+                      "factorisations and sweeps, inner products), %d threads on %s"
+                      % ("/".join(map(str, its)), "/".join("%.1f" % x for x in secs), threads, model),
+            "cpu_model": model}
     print(json.dumps(line))
     if dist is not None:
         dist.destroy_process_group()

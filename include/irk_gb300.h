@@ -64,7 +64,7 @@ enum irk_status {
     IRK_ERR_INVALID = -1,  /* bad argument or pattern */
     IRK_ERR_NOMEM = -2,    /* device or host allocation failed */
     IRK_ERR_SINGULAR = -3, /* zero pivot in a diagonal block of the ILU(0) */
-    IRK_ERR_NONFINITE = -4,/* NaN/Inf in a residual or Krylov quantity */
+    IRK_ERR_NONFINITE = -4,/* NaN/Inf in an input (J, M, R) or a Krylov quantity */
     IRK_ERR_TIMEOUT = -5,  /* a bounded device-side wait gave up */
     IRK_ERR_CUDA = -6,     /* a CUDA runtime call failed */
     IRK_ERR_STATE = -7,    /* call out of order (e.g. apply before factor) */
@@ -150,10 +150,38 @@ typedef struct {
                           (transformed: A^{-1} (x) M - dt diag(J_1..J_s);
                           untransformed: I (x) M - dt [a_kl J_k]).  Not
                           accepted by irk_group_create. */
+    int spin_limit;    /* polls a device-side wait on another thread block
+                          makes before it gives up: the persistent sweep's
+                          waits for published rows and the grid barrier of the
+                          Arnoldi launch.  A wait that gives up records
+                          IRK_ERR_TIMEOUT, lets its own bulk copies land and
+                          leaves the kernel; the call returns IRK_ERR_TIMEOUT
+                          and the context stays usable.  0 (default) = 2^20
+                          polls (about a second); must be >= 0. */
 } irk_options;
 
 /* Fill *opt with the defaults listed above. */
 IRK_API void irk_default_options(irk_options *opt);
+
+/* Magnitude range of the double-float Krylov arithmetic (IRK_KRYLOV_DF64).
+ * A double-float value is a pair of binary32 numbers, so its exponent range
+ * is binary32's: a magnitude above about 3.4e38 overflows, and below about
+ * 1e-31 the low word turns subnormal and the value keeps fewer than 48
+ * significant bits.  The library therefore
+ *   - refuses (IRK_ERR_INVALID, at irk_setup / irk_update_values) a J or M
+ *     whose largest magnitude is neither 0 nor within
+ *     [IRK_DF64_MIN_MAGNITUDE, IRK_DF64_MAX_MAGNITUDE] (2^-100 .. 2^100,
+ *     about 7.9e-31 .. 1.3e30), and (at irk_factor / irk_solve) a dt with
+ *     dt * max|J| above IRK_DF64_MAX_MAGNITUDE;
+ *   - scales every right-hand side (irk_solve, irk_apply_operator,
+ *     irk_apply_precond) by the power of two that brings its largest
+ *     magnitude into [1, 2) before the conversion to double-float, and the
+ *     result back by the inverse power: exact in binary64, so R of any
+ *     finite magnitude is accepted and, away from the binary32 limits, the
+ *     result is bit for bit the unscaled one.
+ * IRK_KRYLOV_FP64 has binary64's range and none of these limits. */
+#define IRK_DF64_MIN_MAGNITUDE 7.888609052210118e-31 /* 2^-100 */
+#define IRK_DF64_MAX_MAGNITUDE 1.2676506002282294e30 /* 2^100 */
 
 /* Create a context for one stage system (Sec. 4.1, eq. big-irk).
  *   s         number of stages, 1 <= s <= 8.
@@ -167,14 +195,19 @@ IRK_API void irk_default_options(irk_options *opt);
  *   opt       NULL = defaults.  The pattern must be structurally symmetric.
  * Copies everything; allocates the Krylov workspace for the given restart.
  * Returns IRK_ERR_INVALID for a malformed pattern (unsorted, missing
- * diagonal, out-of-range column, not symmetric). */
+ * diagonal, out-of-range column, not symmetric) or, with IRK_KRYLOV_DF64,
+ * values outside the double-float range above; IRK_ERR_NONFINITE when J or
+ * M holds a NaN or an infinity (checked while the values are copied in). */
 IRK_API int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t *row_ptr,
               const int32_t *col_idx, const double *J, const double *M, int mem_space,
               const irk_options *opt);
 
 /* Replace the values of J and M (same pattern; J holds s Jacobians when
  * the context was set up with stage_jacobians = 1), e.g. at a new Newton
- * iterate (Sec. 4.1).  Invalidates the factors. */
+ * iterate (Sec. 4.1).  Invalidates the factors.  IRK_ERR_NONFINITE for a NaN
+ * or infinity in J or M, IRK_ERR_INVALID for values outside the
+ * double-float range (IRK_KRYLOV_DF64); the context then holds no usable
+ * values until a later irk_update_values succeeds. */
 IRK_API int irk_update_values(irk_ctx *ctx, const double *J, const double *M, int mem_space);
 
 /* Build the preconditioner for time step dt (once per linear solve,
@@ -245,11 +278,15 @@ IRK_API int irk_apply_precond(irk_ctx *ctx, const double *V, double *Z, int mem_
  * Limits and errors:
  *   - the working set is 16 + 16*w bytes per unknown (w = 1 with FP32/BF16
  *     factors, 2 with FP64 factors) plus 256 bytes; a larger system returns
- *     IRK_ERR_SCRATCH_LIMIT (with FP32 factors: up to 2,097,120 unknowns);
+ *     IRK_ERR_SCRATCH_LIMIT (up to 2,097,120 unknowns with FP32/BF16
+ *     factors, 1,398,080 with FP64 factors);
  *   - IRK_ERR_STATE if the context is not factored; IRK_ERR_INVALID if it has
  *     no preconditioner, uses per-level sweeps (block size > 128,
  *     IRK_SWEEP_LEVELS, or AUTO choosing per-level launches for wide levels),
- *     or belongs to another device than the current one.
+ *     or belongs to another device than the current one;
+ *   - the device error word of the sweep is reported in full: IRK_ERR_SINGULAR,
+ *     IRK_ERR_NONFINITE or IRK_ERR_TIMEOUT (a wait on another thread block
+ *     that gave up, see irk_options.spin_limit), in that order of precedence.
  * Set-up: the first call on a device (with that device current) looks up
  * the array's device address once; make that first call before any stream
  * capture.  The array is shared by every call on a device and keeps the last
@@ -406,6 +443,11 @@ typedef struct {
     int sweep_two_colour;
 } irk_stats;
 IRK_API int irk_get_stats(const irk_ctx *ctx, irk_stats *out);
+
+/* Change irk_options.spin_limit of a live context for the calls that follow
+ * (0 = the default of 2^20 polls).  IRK_ERR_INVALID for a negative value or
+ * a NULL context. */
+IRK_API int irk_set_spin_limit(irk_ctx *ctx, int spin_limit);
 
 /* Change irk_options.timing of a live context (0, 1 or 2) for the calls that
  * follow, e.g. to time a sample of a long run.  Leaving timing = 2 keeps the

@@ -29,8 +29,9 @@ from . import tableau  # noqa: F401  (re-export)
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "irk_oracle.c")
 _LIB = os.path.join(_HERE, "libirk_oracle.so")
+_LIB_OMP = os.path.join(_HERE, "libirk_oracle_omp.so")
 _lock = threading.Lock()
-_lib = None
+_libs = {}
 
 FORM_TRANSFORMED = 0
 FORM_UNTRANSFORMED = 1
@@ -43,21 +44,29 @@ _codes = {0: "ok", 1: "not converged", -1: "invalid argument", -2: "out of memor
           -3: "singular diagonal block", -4: "non-finite value"}
 
 
-def build(force: bool = False) -> str:
-    """Compile irk_oracle.c into libirk_oracle.so next to it (gcc, -O2)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+def build(force: bool = False, omp: bool = False) -> str:
+    """Compile irk_oracle.c next to it (gcc, -O2): libirk_oracle.so (serial),
+    or with omp=True libirk_oracle_omp.so (the same source with -fopenmp)."""
+    out = _LIB_OMP if omp else _LIB
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + ".%d.tmp" % os.getpid()
+        extra = ["-fopenmp"] if omp else []
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
 
 
-def _load():
-    global _lib
+def threads(n: int = 0) -> int:
+    """Threads of the multi-core build (n > 0 sets them); returns the count
+    its parallel regions use."""
+    return int(_load(True).irk_ref_threads(int(n)))
+
+
+def _load(omp=False):
     with _lock:
-        if _lib is None:
-            build()
-            lib = ctypes.CDLL(_LIB)
+        if omp not in _libs:
+            path = build(omp=omp)
+            lib = ctypes.CDLL(path)
             P = ctypes.c_void_p
             I, L, D = ctypes.c_int, ctypes.c_long, ctypes.c_double
             lib.irk_ref_apply_transformed.argtypes = [I, P, I, I, P, P, P, L, P, D, P, P]
@@ -83,8 +92,9 @@ def _load():
             lib.irk_ref_solve_ordered.argtypes = [I, P, I, I, P, P, P, L, P, D, P, P, P, I, I, D, P, P, P,
                                                   P, P]
             lib.irk_ref_precond_apply_ordered.argtypes = [I, P, I, I, P, P, P, L, P, D, P, P, P, P, P]
-            _lib = lib
-    return _lib
+            lib.irk_ref_threads.argtypes = [I]
+            _libs[omp] = lib
+    return _libs[omp]
 
 
 def _p(a):
@@ -108,7 +118,10 @@ def _check(rc, what):
 class Problem:
     """Host copy of one stage system: pattern, J (shared or per stage), M."""
 
-    def __init__(self, s, T, m, row_ptr, col_idx, J, M, A=None):
+    def __init__(self, s, T, m, row_ptr, col_idx, J, M, A=None, omp=False):
+        """omp=True: run apply / solve / precond_apply in the multi-core build
+        (same source and algorithm, independent work spread over threads)."""
+        self.omp = bool(omp)
         self.s, self.T, self.m = int(s), int(T), int(m)
         self.row_ptr = _i32(row_ptr)
         self.col_idx = _i32(col_idx)
@@ -137,7 +150,7 @@ class Problem:
 
     def apply(self, X, dt, form=FORM_TRANSFORMED):
         """Y = B X (form 0, eq. big-irk) or the untransformed product (form 1)."""
-        lib = _load()
+        lib = _load(self.omp)
         X = _f64(X).reshape(-1)
         Y = np.empty_like(X)
         rp, ci, J, js, M = self._args()
@@ -152,7 +165,7 @@ class Problem:
     def solve(self, R, dt, rtol=1e-8, form=FORM_TRANSFORMED, precond=PC_UNCOUPLED, shift=None,
               restart=30, max_iter=3000, x0=None, history=False):
         """FGMRES(restart) solve; returns dict(x, iters, relres, cycles, rc[, est])."""
-        lib = _load()
+        lib = _load(self.omp)
         R = _f64(R).reshape(-1)
         X = np.zeros_like(R) if x0 is None else _f64(x0).reshape(-1).copy()
         it = ctypes.c_int(0)
@@ -173,7 +186,7 @@ class Problem:
 
     def precond_apply(self, v, dt, form=FORM_TRANSFORMED, precond=PC_UNCOUPLED, shift=None):
         """z = P^{-1} v for a freshly built preconditioner."""
-        lib = _load()
+        lib = _load(self.omp)
         v = _f64(v).reshape(-1)
         z = np.empty_like(v)
         sh = None if shift is None else _f64(shift)

@@ -24,10 +24,25 @@
  *
  * Return codes: 0 ok, 1 not converged, -1 bad argument, -2 out of memory,
  * -3 singular diagonal block, -4 non-finite value.
+ *
+ * Multi-core build.  Compiled with -fopenmp (libirk_oracle_omp.so) the same
+ * source spreads independent work over threads: the operator's block rows
+ * (every (stage, element) row of Sec. 4.1 is computed on its own), the
+ * stages of the uncoupled preconditioner (the s independent factorisations
+ * and sweeps of Sec. 4.3.2, the paper's stage parallelism of Sec. 4.5), the
+ * element blocks of its assembly, and the vector operations and inner
+ * products of FGMRES.  Every row, block and factor is computed by the same
+ * operations in the same order as in the serial build; only the inner
+ * products' partial sums are added in a different order.  Without
+ * -fopenmp (libirk_oracle.so, the build the tests check) the pragmas are
+ * ignored and everything runs serially.
  */
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define REF_OK 0
 #define REF_NOT_CONVERGED 1
@@ -169,9 +184,10 @@ int irk_ref_apply_transformed(int s, const double *Ainv, int T, int m,
     if (s < 1 || T < 0 || m < 1) return REF_EINVAL;
     long n = (long)T * m;
     long mm = (long)m * m;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < s; ++k) {
-        const double *Jk = J + k * jstride;
         for (int i = 0; i < T; ++i) {
+            const double *Jk = J + k * jstride;
             double *y = Y + k * n + (long)i * m;
             for (int a = 0; a < m; ++a) y[a] = 0.0;
             for (int l = 0; l < s; ++l)
@@ -194,9 +210,10 @@ int irk_ref_apply_untransformed(int s, const double *A, int T, int m,
     if (s < 1 || T < 0 || m < 1) return REF_EINVAL;
     long n = (long)T * m;
     long mm = (long)m * m;
+#pragma omp parallel for collapse(2) schedule(static)
     for (int k = 0; k < s; ++k) {
-        const double *Jk = J + k * jstride;
         for (int i = 0; i < T; ++i) {
+            const double *Jk = J + k * jstride;
             double *y = Y + k * n + (long)i * m;
             for (int a = 0; a < m; ++a) y[a] = 0.0;
             mat_vec_add(m, 1.0, M + i * mm, K + k * n + (long)i * m, y);
@@ -490,6 +507,7 @@ void irk_ref_assemble_shifted(int T, int m, const int *row_ptr, const int *col_i
                               double *out_vals)
 {
     long mm = (long)m * m;
+#pragma omp parallel for schedule(static)
     for (int i = 0; i < T; ++i)
         for (long p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
             for (long e = 0; e < mm; ++e)
@@ -506,8 +524,21 @@ typedef void (*ref_op_fn)(void *ctx, const double *x, double *y);
 static double dot(long N, const double *a, const double *b)
 {
     double acc = 0.0;
+#pragma omp parallel for reduction(+ : acc) schedule(static)
     for (long q = 0; q < N; ++q) acc += a[q] * b[q];
     return acc;
+}
+
+/* Threads the multi-core build uses (n > 0 sets them); 1 in the serial build. */
+int irk_ref_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }
 
 /* Restarted flexible GMRES with modified Gram-Schmidt and Givens rotations,
@@ -544,6 +575,7 @@ int irk_ref_fgmres(long N, ref_op_fn apply_A, void *actx, ref_op_fn apply_P, voi
         goto done;
     }
     apply_A(actx, x, r);
+#pragma omp parallel for schedule(static)
     for (long q = 0; q < N; ++q) r[q] = b[q] - r[q];
     beta = sqrt(dot(N, r, r));
     if (est_hist) est_hist[0] = beta / bnorm;
@@ -552,6 +584,7 @@ int irk_ref_fgmres(long N, ref_op_fn apply_A, void *actx, ref_op_fn apply_P, voi
         if (beta <= rtol * bnorm) break;
         if (total >= max_iter) { rc = REF_NOT_CONVERGED; break; }
         ++cycles;
+#pragma omp parallel for schedule(static)
         for (long q = 0; q < N; ++q) V[q] = r[q] / beta;
         for (int q = 0; q <= R; ++q) g[q] = 0.0;
         g[0] = beta;
@@ -563,12 +596,15 @@ int irk_ref_fgmres(long N, ref_op_fn apply_A, void *actx, ref_op_fn apply_P, voi
             for (int i = 0; i <= j; ++i) {
                 double h = dot(N, w, V + (long)i * N);
                 H[i * R + j] = h;
+#pragma omp parallel for schedule(static)
                 for (long q = 0; q < N; ++q) w[q] -= h * V[(long)i * N + q];
             }
             double hnext = sqrt(dot(N, w, w));
             H[(j + 1) * R + j] = hnext;
-            if (hnext != 0.0)
+            if (hnext != 0.0) {
+#pragma omp parallel for schedule(static)
                 for (long q = 0; q < N; ++q) w[q] /= hnext;
+            }
             /* previous rotations on the new column */
             for (int i = 0; i < j; ++i) {
                 double t = cs[i] * H[i * R + j] + sn[i] * H[(i + 1) * R + j];
@@ -597,9 +633,12 @@ int irk_ref_fgmres(long N, ref_op_fn apply_A, void *actx, ref_op_fn apply_P, voi
             for (int k = i + 1; k <= jlast; ++k) acc -= H[i * R + k] * y[k];
             y[i] = acc / H[i * R + i];
         }
-        for (int i = 0; i <= jlast; ++i)
+        for (int i = 0; i <= jlast; ++i) {
+#pragma omp parallel for schedule(static)
             for (long q = 0; q < N; ++q) x[q] += y[i] * Z[(long)i * N + q];
+        }
         apply_A(actx, x, r);
+#pragma omp parallel for schedule(static)
         for (long q = 0; q < N; ++q) r[q] = b[q] - r[q];
         beta = sqrt(dot(N, r, r));
     }
@@ -660,6 +699,7 @@ static void ref_precond_apply(void *ctx, const double *v, double *z)
     if (p->kind == REF_PC_NONE) {
         memcpy(z, v, sizeof(double) * N);
     } else if (p->kind == REF_PC_UNCOUPLED) {
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < p->s; ++k)
             irk_ref_bilu0_apply(p->T, p->m, p->rp, p->ci, p->vals + k * p->nnzb * mm,
                                 p->dlu + (long)k * p->T * mm, p->dpiv + (long)k * p->T * p->m,
@@ -720,14 +760,17 @@ static int ref_precond_build(ref_precond *p, int kind, int form, int s, const do
         p->dlu = (double *)malloc(sizeof(double) * s * T * mm);
         p->dpiv = (int *)malloc(sizeof(int) * s * T * m);
         if (!p->vals || !p->dlu || !p->dpiv) return REF_ENOMEM;
+        int rcs[64];
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < s; ++k) {
             double *vk = p->vals + k * nnzb * mm;
             irk_ref_assemble_shifted(T, m, row_ptr, col_idx, J + k * jstride, M,
                                      Ainv[k * s + k] + alpha[k], dt, vk);
-            int rc = irk_ref_bilu0(T, m, row_ptr, col_idx, vk, p->dlu + (long)k * T * mm,
+            rcs[k] = irk_ref_bilu0(T, m, row_ptr, col_idx, vk, p->dlu + (long)k * T * mm,
                                    p->dpiv + (long)k * T * m);
-            if (rc != REF_OK) return rc;
         }
+        for (int k = 0; k < s; ++k)
+            if (rcs[k] != REF_OK) return rcs[k];
         return REF_OK;
     }
     if (kind == REF_PC_STAGE_MAJOR) {

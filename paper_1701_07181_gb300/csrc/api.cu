@@ -160,9 +160,17 @@ int sync_err(irk_ctx *c) {
     return err_code(*herr);
 }
 
+// A largest magnitude the double-float arithmetic can carry: 0 or within
+// [2^-100, 2^100] (include/irk_gb300.h).
+bool df_range_ok(double amax) {
+    return amax == 0.0 || (amax >= IRK_DF64_MIN_MAGNITUDE && amax <= IRK_DF64_MAX_MAGNITUDE);
+}
+
 // Load J and M (row-major binary64 in mem_space) into the context's
-// column-major device blocks, through the staging buffer d_io when small
-// enough, else through a temporary device buffer.
+// column-major device blocks through a temporary device buffer.  The
+// conversion records the largest magnitude of each and flags non-finite
+// values: IRK_ERR_NONFINITE for a NaN or infinity, IRK_ERR_INVALID for
+// double-float values out of range.
 int load_values(irk_ctx *c, const double *J, const double *M, int mem_space) {
     const long long mm = (long long)c->m * c->m;
     const long long nJ = (long long)c->nJ * c->nnzb * mm, nM = (long long)c->T * mm;
@@ -170,13 +178,45 @@ int load_values(irk_ctx *c, const double *J, const double *M, int mem_space) {
     double *tmp = nullptr;
     int rc = cuda_status(cudaMalloc(&tmp, (size_t)need * sizeof(double)));
     if (rc) return rc;
-    if ((rc = copy_in(tmp, J, (size_t)nJ * sizeof(double), mem_space, c->stream)) == IRK_OK &&
-        (rc = launch_convert_blocks(c, tmp, c->d_J, (long long)c->nJ * c->nnzb)) == IRK_OK &&
+    unsigned long long *amax = c->d_amax;  // [0] J, [1] M
+    unsigned long long *hmax = reinterpret_cast<unsigned long long *>(c->h_scal + 4);
+    int *herr = reinterpret_cast<int *>(c->h_scal + 3);
+    if ((rc = cuda_status(cudaMemsetAsync(amax, 0, 2 * sizeof(unsigned long long), c->stream))) == IRK_OK &&
+        (rc = cuda_status(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream))) == IRK_OK &&
+        (rc = copy_in(tmp, J, (size_t)nJ * sizeof(double), mem_space, c->stream)) == IRK_OK &&
+        (rc = launch_convert_blocks(c, tmp, c->d_J, (long long)c->nJ * c->nnzb, amax, c->d_err)) == IRK_OK &&
         (rc = copy_in(tmp, M, (size_t)nM * sizeof(double), mem_space, c->stream)) == IRK_OK &&
-        (rc = launch_convert_blocks(c, tmp, c->d_M, c->T)) == IRK_OK)
+        (rc = launch_convert_blocks(c, tmp, c->d_M, c->T, amax + 1, c->d_err)) == IRK_OK &&
+        (rc = cuda_status(cudaMemcpyAsync(hmax, amax, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                          c->stream))) == IRK_OK &&
+        (rc = cuda_status(cudaMemcpyAsync(herr, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream))) == IRK_OK)
         rc = cuda_status(cudaStreamSynchronize(c->stream));
     cudaFree(tmp);
-    return rc;
+    if (rc) return rc;
+    if (*herr & IRK_DEV_ERR_NONFINITE) return IRK_ERR_NONFINITE;
+    double jm, mmx;
+    memcpy(&jm, &hmax[0], sizeof(double));
+    memcpy(&mmx, &hmax[1], sizeof(double));
+    c->jmax = jm;
+    c->mmax = mmx;
+    if (c->df && (!df_range_ok(jm) || !df_range_ok(mmx))) return IRK_ERR_INVALID;
+    return IRK_OK;
+}
+
+// dt admissible for the context's arithmetic: finite, and with double-float
+// dt * max|J| within its range.
+bool dt_ok(const irk_ctx *c, double dt) {
+    if (!std::isfinite(dt)) return false;
+    return !c->df || std::fabs(dt) * c->jmax <= IRK_DF64_MAX_MAGNITUDE;
+}
+
+// Power-of-two scale of a double-float right-hand side in d_io (see the
+// header); null for binary64 (no scaling).
+const double *rhs_scale(irk_ctx *c, int *rc) {
+    if (!c->df) return nullptr;
+    *rc = launch_pow2_scale(c->stream, c->N, c->d_io, c->d_amax + 2, c->d_vscale);
+    c->launches += 2;
+    return c->d_vscale;
 }
 
 }  // namespace
@@ -306,6 +346,8 @@ void free_ctx(irk_ctx *c) {
     cudaFree(c->d_part);
     cudaFree(c->d_ticket);
     cudaFree(c->d_err);
+    cudaFree(c->d_vscale);
+    cudaFree(c->d_amax);
     if (c->h_scal) cudaFreeHost(c->h_scal);
     delete c;
 }
@@ -334,6 +376,7 @@ void irk_default_options(irk_options *o) {
     o->partitions = 0;
     o->partition = nullptr;
     o->stage_jacobians = 0;
+    o->spin_limit = 0;
 }
 
 const char *irk_strerror(int code) {
@@ -372,7 +415,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
         c->opt.factor_prec > IRK_FACTOR_BF16 || c->opt.krylov_arith < 0 || c->opt.krylov_arith > 1 ||
         c->opt.formulation < 0 || c->opt.formulation > 1 || c->opt.sweep < 0 || c->opt.sweep > 1 ||
         c->opt.ordering < 0 || c->opt.ordering > 1 || c->opt.partitions < 0 || c->opt.stage_jacobians < 0 ||
-        c->opt.stage_jacobians > 1 ||
+        c->opt.stage_jacobians > 1 || c->opt.spin_limit < 0 ||
         (c->opt.precond == IRK_PC_UNCOUPLED && c->opt.formulation != IRK_TRANSFORMED)) {
         delete c;
         return IRK_ERR_INVALID;
@@ -384,6 +427,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
     c->df = c->opt.krylov_arith == IRK_KRYLOV_DF64;
     c->fprec = c->opt.factor_prec;
     c->nJ = (c->opt.stage_jacobians && s > 1) ? s : 1;
+    c->spin = c->opt.spin_limit > 0 ? c->opt.spin_limit : IRK_DEFAULT_SPIN_LIMIT;
     cudaGetDevice(&c->dev);
     // pattern: host copy and validation
     c->h_rp.resize(T + 1);
@@ -472,6 +516,8 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
               cudaMalloc(&c->d_part, sizeof(vec8) * IRK_PART_SLOTS) == cudaSuccess &&
               cudaMalloc(&c->d_ticket, 4 * sizeof(unsigned int)) == cudaSuccess &&
               cudaMalloc(&c->d_err, sizeof(int)) == cudaSuccess &&
+              cudaMalloc(&c->d_vscale, 2 * sizeof(double)) == cudaSuccess &&
+              cudaMalloc(&c->d_amax, 4 * sizeof(unsigned long long)) == cudaSuccess &&
               cudaMallocHost(&c->h_scal, 4 * IRK_SCAL_BYTES) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
@@ -501,7 +547,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
 }
 
 int irk_update_values(irk_ctx *c, const double *J, const double *M, int mem_space) {
-    if (!c || !J || !M) return IRK_ERR_INVALID;
+    if (!c || !J || !M || (mem_space != IRK_HOST && mem_space != IRK_DEVICE)) return IRK_ERR_INVALID;
     c->factored = false;
     return load_values(c, J, M, mem_space);
 }
@@ -530,7 +576,7 @@ static void factor_finish(irk_ctx *c, double dt, int rc, cudaEvent_t e0, cudaEve
 }
 
 int irk_factor(irk_ctx *c, double dt) {
-    if (!c || !std::isfinite(dt)) return IRK_ERR_INVALID;
+    if (!c || !dt_ok(c, dt)) return IRK_ERR_INVALID;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -543,12 +589,14 @@ int irk_factor(irk_ctx *c, double dt) {
 }
 
 int irk_apply_operator(irk_ctx *c, const double *X, double *Y, double dt, int mem_space) {
-    if (!c || !X || !Y) return IRK_ERR_INVALID;
+    if (!c || !X || !Y || !dt_ok(c, dt)) return IRK_ERR_INVALID;
     vec8 *xi = c->d_V, *yi = c->d_V + c->N;
-    int rc;
+    int rc = IRK_OK;
+    const double *sc = nullptr;
     if ((rc = copy_in(c->d_io, X, sizeof(double) * c->N, mem_space, c->stream)) ||
-        (rc = launch_to_internal(c, c->d_io, xi)) || (rc = launch_matvec(c, xi, yi, nullptr, dt, 0)) ||
-        (rc = launch_to_external(c, yi, c->d_io)) ||
+        ((sc = rhs_scale(c, &rc)), rc) ||
+        (rc = launch_to_internal(c, c->d_io, xi, sc)) || (rc = launch_matvec(c, xi, yi, nullptr, dt, 0)) ||
+        (rc = launch_to_external(c, yi, c->d_io, sc)) ||
         (rc = copy_out(Y, c->d_io, sizeof(double) * c->N, mem_space, c->stream)))
         return rc;
     return cuda_status(cudaStreamSynchronize(c->stream));
@@ -558,18 +606,21 @@ int irk_apply_precond(irk_ctx *c, const double *V, double *Z, int mem_space) {
     if (!c || !V || !Z) return IRK_ERR_INVALID;
     if (!c->factored && c->opt.precond != IRK_PC_NONE) return IRK_ERR_STATE;
     vec8 *vi = c->d_V, *zi = c->d_Z;
-    int rc;
+    int rc = IRK_OK;
+    const double *sc = nullptr;
+    cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
     if ((rc = copy_in(c->d_io, V, sizeof(double) * c->N, mem_space, c->stream)) ||
-        (rc = launch_to_internal(c, c->d_io, vi)) || (rc = pc_apply(c, vi, zi)) ||
-        (rc = launch_to_external(c, zi, c->d_io)) ||
+        ((sc = rhs_scale(c, &rc)), rc) ||
+        (rc = launch_to_internal(c, c->d_io, vi, sc)) || (rc = pc_apply(c, vi, zi)) ||
+        (rc = launch_to_external(c, zi, c->d_io, sc)) ||
         (rc = copy_out(Z, c->d_io, sizeof(double) * c->N, mem_space, c->stream)))
         return rc;
-    return cuda_status(cudaStreamSynchronize(c->stream));
+    return sync_err(c);
 }
 
 int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, int mem_space, int *iters,
               double *relres) {
-    if (!c || !Rhs || !W || !(rtol >= 0.0) || !std::isfinite(dt)) return IRK_ERR_INVALID;
+    if (!c || !Rhs || !W || !(rtol >= 0.0) || !dt_ok(c, dt)) return IRK_ERR_INVALID;
     int rc;
     const long long l0 = c->launches;  // counts the refactorisation too, if any
     cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream);
@@ -613,7 +664,9 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     int total = 0, cycles = 0;
     double bnorm = 0.0, beta = 0.0;
     rc = r_in ? IRK_OK : copy_in(c->d_io, Rhs, sizeof(double) * N, mem_space, c->stream);
-    if (!rc) rc = launch_to_internal(c, c->d_io, c->d_b);
+    const double *sc = nullptr;
+    if (!rc) sc = rhs_scale(c, &rc);
+    if (!rc) rc = launch_to_internal(c, c->d_io, c->d_b, sc);
     if (!rc) rc = launch_axpy_dot_slot(c, c->d_b, nullptr, 0, nullptr, 1, 1, 0, nullptr);
     if (!rc) rc = cuda_status(cudaMemcpyAsync(beta_h, irk_beta_ptr(c), sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     if (!rc) rc = sync_err(c);
@@ -709,7 +762,7 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     }
     if (rc == IRK_OK || rc == IRK_NOT_CONVERGED) {
         int rc2;
-        if ((rc2 = launch_to_external(c, c->d_x, c->d_io)) ||
+        if ((rc2 = launch_to_external(c, c->d_x, c->d_io, sc)) ||
             (rc2 = copy_out(W, c->d_io, sizeof(double) * N, mem_space, c->stream)) ||
             (rc2 = cuda_status(cudaStreamSynchronize(c->stream))))
             rc = rc2;
@@ -805,6 +858,13 @@ int irk_step_outputs(irk_ctx *c, const double *W, const double *b, const double 
     const int rs = cuda_status(cudaStreamSynchronize(c->stream));
     cudaFree(tmp);
     return rc != IRK_OK ? rc : rs;
+}
+
+int irk_set_spin_limit(irk_ctx *c, int spin_limit) {
+    if (!c || spin_limit < 0) return IRK_ERR_INVALID;
+    c->opt.spin_limit = spin_limit;
+    c->spin = spin_limit > 0 ? spin_limit : IRK_DEFAULT_SPIN_LIMIT;
+    return IRK_OK;
 }
 
 int irk_set_timing(irk_ctx *c, int timing) {

@@ -708,7 +708,7 @@ int launch_g_sweep(irk_group *g) {
     return ilu_sweep_group(g->stream, g->dev, g->fprec, g->df, g->n_items, g->m, g->max_item_blocks, g->d_lo,
                            g->d_up, g->d_prp, g->d_pci, g->d_pvoff, g->d_vals, g->d_dinv, g->d_pool, g->d_ll,
                            ++g->epoch, g->d_err, g->d_lane_of_prow, g->d_sw, g->d_sw + Lm, g->d_sw + 2 * Lm,
-                           g->d_sw + 3 * Lm);
+                           g->d_sw + 3 * Lm, g->opt.spin_limit > 0 ? g->opt.spin_limit : IRK_DEFAULT_SPIN_LIMIT);
 }
 
 }  // namespace
@@ -849,7 +849,8 @@ int irk_group_create(irk_group **out, int s, const double *A, int m, int max_ele
     if ((o.precond != IRK_PC_UNCOUPLED && o.precond != IRK_PC_NONE) || o.formulation != IRK_TRANSFORMED ||
         (o.factor_prec != IRK_FACTOR_FP32 && o.factor_prec != IRK_FACTOR_FP64) || o.krylov_arith < 0 ||
         o.krylov_arith > 1 || o.restart < 1 || o.restart > IRK_MAX_RESTART || o.partitions > 1 ||
-        (opt && opt->partition) || o.ordering < 0 || o.ordering > 1 || m > 128 || o.stage_jacobians != 0) {
+        (opt && opt->partition) || o.ordering < 0 || o.ordering > 1 || m > 128 || o.stage_jacobians != 0 ||
+        o.spin_limit < 0) {
         delete g;
         return IRK_ERR_INVALID;
     }

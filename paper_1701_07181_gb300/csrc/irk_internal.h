@@ -16,6 +16,10 @@
 #define IRK_DEV_ERR_NONFINITE 2
 #define IRK_DEV_ERR_TIMEOUT 4
 
+// Polls a wait on another thread block makes before giving up (the default
+// of irk_options.spin_limit).
+#define IRK_DEFAULT_SPIN_LIMIT (1 << 20)
+
 // Element type of every Krylov vector: 8 bytes, either a binary64 or a
 // double-float pair (hi, lo).  Vectors are stored element-interleaved:
 // index (i*s + k)*m + a for element i, stage k, component a.
@@ -108,6 +112,12 @@ struct irk_ctx {
     unsigned int *d_ticket = nullptr;
     unsigned int *d_gbar = nullptr;  // grid-barrier words of k_arnoldi (in d_ticket's allocation)
     int *d_err = nullptr;
+    // power-of-two scaling of double-float right-hand sides: [0] the factor
+    // applied on the way in, [1] its inverse on the way out
+    double *d_vscale = nullptr;
+    unsigned long long *d_amax = nullptr;  // |x| bits of the largest magnitude seen
+    double jmax = 0.0, mmax = 0.0;         // largest magnitudes of J and M
+    int spin = IRK_DEFAULT_SPIN_LIMIT;     // effective irk_options.spin_limit
     int red_blocks = 0;
     irk_stats stats;
     long long launches = 0;
@@ -137,11 +147,20 @@ int irk_allow_max_smem(const void *func);
 // phase timing marks (api.cu): no-ops unless irk_options.timing
 int tmark_begin(irk_ctx *c);
 void tmark_end(irk_ctx *c, int slot, int kind);
-// stage-major binary64 <-> element-interleaved vec8
-int launch_to_internal(irk_ctx *c, const double *src, vec8 *dst);
-int launch_to_external(irk_ctx *c, const vec8 *src, double *dst);
-// J/M (row-major binary64, device) -> internal column-major vec8 blocks
-int launch_convert_blocks(irk_ctx *c, const double *src, vec8 *dst, long long nblocks);
+// stage-major binary64 <-> element-interleaved vec8; scale (device pair or
+// null): the way in multiplies by scale[0], the way out by scale[1]
+int launch_to_internal(irk_ctx *c, const double *src, vec8 *dst, const double *scale = nullptr);
+int launch_to_external(irk_ctx *c, const vec8 *src, double *dst, const double *scale = nullptr);
+int launch_to_internal_on(cudaStream_t st, const irk_ctx *c, const double *src, vec8 *dst, const double *scale);
+int launch_to_external_on(cudaStream_t st, const irk_ctx *c, const vec8 *src, double *dst, const double *scale);
+// scale[0..1] = (2^-e, 2^e) with 2^e <= max_q |src[q]| < 2^(e+1) (1, 1 for a
+// zero or non-finite maximum); amax is a device word used as scratch
+int launch_pow2_scale(cudaStream_t st, long long n, const double *src, unsigned long long *amax, double *scale);
+// J/M (row-major binary64, device) -> internal column-major vec8 blocks;
+// records the largest |value| (as binary64 bits) in *amax and raises
+// IRK_DEV_ERR_NONFINITE in *err for a NaN or infinity
+int launch_convert_blocks(irk_ctx *c, const double *src, vec8 *dst, long long nblocks, unsigned long long *amax,
+                          int *err);
 
 // ---- launchers (k_krylov.cu) ----
 // Scalars live in 32-byte slots of c->d_scal (128 slots): 0 = norm results,
@@ -187,7 +206,7 @@ int ilu_sweep_group(cudaStream_t st, int dev, int fprec, int df, int nitems, int
                     const int *lo, const int *up, const int *rp, const int *ci, const int *voff, const void *vals,
                     const void *dinv, vec8 *vpool, unsigned long long *llpool, int ep, int *err,
                     const int *lane_of_row, const long long *vin, const long long *zout, const long long *yll,
-                    const long long *zll);
+                    const long long *zll, int spin);
 
 // ---- helpers (api.cu) ----
 int cuda_status(cudaError_t e);

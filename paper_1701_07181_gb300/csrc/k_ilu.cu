@@ -1519,8 +1519,10 @@ __global__ void __launch_bounds__(256) k_sweep_bu(const int *rows0, int nrows, i
 // it reads are published (per-row flags set to this application's epoch),
 // computes its row and publishes it.  Every dependency sits earlier in the
 // list, so the lowest unfinished item can always proceed.  Waits are bounded:
-// after IRK_SPIN_LIMIT polls, or as soon as another warp reported a timeout,
-// the warp records IRK_DEV_ERR_TIMEOUT and leaves.
+// after `spin` polls (irk_options.spin_limit), or as soon as another warp
+// reported an error, the warp records IRK_DEV_ERR_TIMEOUT (the first case),
+// waits for its own bulk copies still in flight (bounded by the fixed
+// IRK_SPIN_LIMIT of a copy's completion) and leaves.
 #define IRK_PB 4  // values per lane: b <= 128
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
@@ -1531,24 +1533,6 @@ __device__ __forceinline__ int ld_acquire(const int *p) {
 
 __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Called by all 32 lanes of a warp; the decision is warp-uniform (every lane
-// polls with acquire semantics, the loop exits for all lanes together).
-__device__ __forceinline__ bool wait_epoch(const int *flag, int ep, int *err) {
-    for (int spins = 0;; ++spins) {
-        const int v = ld_acquire(flag);
-        if (__all_sync(0xffffffffu, v == ep)) return true;
-        if (spins > 32) __nanosleep(64);
-        if ((spins & 255) == 255) {
-            const int e = ld_acquire(err);
-            if (__any_sync(0xffffffffu, e != 0)) return false;
-        }
-        if (spins > IRK_SPIN_LIMIT) {
-            if ((threadIdx.x & 31) == 0) atomicOr(err, IRK_DEV_ERR_TIMEOUT);
-            return false;
-        }
-    }
 }
 
 __device__ __forceinline__ float ldcg_c(const float *p) { return __ldcg(p); }
@@ -1620,7 +1604,8 @@ struct LL<double> {
 // Poll the b published values of one row (lane holds entries lane + 32u);
 // warp-uniform, bounded, abortable.  Returns false on timeout / abort.
 template <class C>
-__device__ __forceinline__ bool ll_wait_row(const unsigned long long *row, int b, int ep, int *err, C (&out)[IRK_PB]) {
+__device__ __forceinline__ bool ll_wait_row(const unsigned long long *row, int b, int ep, int *err, int spin,
+                                            C (&out)[IRK_PB]) {
     const int lane = threadIdx.x & 31;
     for (int spins = 0;; ++spins) {
         bool ok = true;
@@ -1636,7 +1621,7 @@ __device__ __forceinline__ bool ll_wait_row(const unsigned long long *row, int b
             const int e = ld_acquire(err);
             if (__any_sync(0xffffffffu, e != 0)) return false;
         }
-        if (spins > IRK_SPIN_LIMIT) {
+        if (spins >= spin) {
             if (lane == 0) atomicOr(err, IRK_DEV_ERR_TIMEOUT);
             return false;
         }
@@ -1662,7 +1647,7 @@ __global__ void __launch_bounds__(128) k_sweep_staged(int nb, int b, int NS, con
                                                       const int *rp, const int *ci, const int *voff, const F *vals,
                                                       const F *dinv, const vec8 *v, unsigned long long *yll,
                                                       unsigned long long *zll, vec8 *z, int ep, int *err,
-                                                      SweepLanes lanes) {
+                                                      SweepLanes lanes, int spin) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     const int bb = b * b;
@@ -1731,7 +1716,7 @@ __global__ void __launch_bounds__(128) k_sweep_staged(int nb, int b, int NS, con
                 int a = lane + 32 * u;
                 acc[u] = (a < b) ? CT<C>::template from_vec<AR>(AR::ld(v + vo + a)) : C(0);
             }
-        } else if (!ll_wait_row<C>(yll + (long long)vo * LW, b, ep, err, acc)) {
+        } else if (!ll_wait_row<C>(yll + (long long)vo * LW, b, ep, err, spin, acc)) {
             drain();
             return;
         }
@@ -1742,7 +1727,7 @@ __global__ void __launch_bounds__(128) k_sweep_staged(int nb, int b, int NS, con
             C dep[IRK_PB];
             if (!is_dinv) {
                 const int col = fwd ? ci[pbeg + kk] : ci[pend - 1 - kk];
-                if (!ll_wait_row<C>((fwd ? yll : zll) + (long long)voff[col] * LW, b, ep, err, dep)) {
+                if (!ll_wait_row<C>((fwd ? yll : zll) + (long long)voff[col] * LW, b, ep, err, spin, dep)) {
                     drain();
                     return;
                 }
@@ -2337,7 +2322,8 @@ static int apply_persistent(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, c
     unsigned long long *yll = P.d_yll, *zll = P.d_zll;
     int *err = c->d_err;
     SweepLanes none = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &vo, &vals, &dinv, &v, &yll, &zll, &z, &ep, &err, &none};
+    int spin = c->spin;
+    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &vo, &vals, &dinv, &v, &yll, &zll, &z, &ep, &err, &none, &spin};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)kern, P.coop_blocks, threads, args, smem, c->stream);
     c->launches++;
     return cuda_status(e);
@@ -2471,7 +2457,8 @@ int pc_apply(irk_ctx *c, const vec8 *v, vec8 *z) {
 // irk_apply_precond_noalloc: the preconditioner application with its working
 // vectors in a fixed device array instead of context-owned buffers, for
 // callers that cannot allocate (see the header).  Layout of the array:
-// [error word | 256 B] [V internal | N vec8] [Z internal | N vec8]
+// [header | 256 B: error word at 0, |x| maximum at 64, scale pair at 128]
+// [V internal | N vec8] [Z internal | N vec8]
 // [forward words | N*w] [backward words | N*w], each region 256-byte aligned.
 static __device__ __align__(256) unsigned char irk_noalloc_scratch[IRK_NOALLOC_SCRATCH_BYTES];
 
@@ -2483,20 +2470,31 @@ std::mutex g_noalloc_mutex;
 
 size_t na_align(size_t x) { return (x + 255) / 256 * 256; }
 
-template <class AR>
-__global__ void k_na_in(long long N, int T, int m, int s, const double *__restrict__ src, vec8 *dst) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
-        long long a = e % m, r = e / m, k = r % s, i = r / s;
-        AR::st(dst + e, AR::from_double(src[(k * T + i) * m + a]));
-    }
-}
+// Cooperative grid of the persistent sweep for one (kernel, CTA size, shared
+// memory) on one device, computed once (the occupancy query is not free).
+struct NaGrid {
+    const void *kern;
+    int dev, threads;
+    size_t smem;
+    int grid;
+};
+#define IRK_NOALLOC_GRIDS 256
+NaGrid g_na_grids[IRK_NOALLOC_GRIDS];  // fixed table (no host allocation), guarded by g_noalloc_mutex
+int g_na_ngrids = 0;
 
-template <class AR>
-__global__ void k_na_out(long long N, int T, int m, int s, const vec8 *__restrict__ src, double *dst) {
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
-        long long a = e % m, r = e / m, k = r % s, i = r / s;
-        dst[(k * T + i) * m + a] = AR::to_double(AR::ld(src + e));
+int na_grid(const void *kern, int dev, int threads, size_t smem) {
+    std::lock_guard<std::mutex> g(g_noalloc_mutex);
+    for (int q = 0; q < g_na_ngrids; ++q) {
+        const NaGrid &e = g_na_grids[q];
+        if (e.kern == kern && e.dev == dev && e.threads == threads && e.smem == smem) return e.grid;
     }
+    if (allow_max_smem(kern)) return -1;
+    int per_sm = 0, sms = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm <= 0)
+        return -1;
+    if (g_na_ngrids < IRK_NOALLOC_GRIDS) g_na_grids[g_na_ngrids++] = {kern, dev, threads, smem, per_sm * sms};
+    return per_sm * sms;
 }
 
 template <class AR, class C, class F>
@@ -2512,16 +2510,12 @@ int na_sweep(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv, u
     const int threads = 32 * warps;
     const size_t smem = warp_bytes * warps;
     if (smem > 227 * 1024) return IRK_ERR_INVALID;
-    if (allow_max_smem((const void *)kern)) return IRK_ERR_CUDA;
-    int per_sm = 0, sms = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem) != cudaSuccess ||
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->dev) != cudaSuccess || per_sm <= 0)
-        return IRK_ERR_CUDA;
-    int grid = per_sm * sms;
-    int nb = P.nb, b = P.b, ep = 1;
+    int grid = na_grid((const void *)kern, c->dev, threads, smem);
+    if (grid <= 0) return IRK_ERR_CUDA;
+    int nb = P.nb, b = P.b, ep = 1, spin = c->spin;
     const int *lo = P.d_lo_rows, *up = P.d_up_rows, *rp = P.d_rp, *ci = P.d_ci, *vo = P.d_voff;
     SweepLanes none = {nullptr, nullptr, nullptr, nullptr, nullptr};
-    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &vo, &vals, &dinv, &v, &yll, &zll, &z, &ep, &err, &none};
+    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &vo, &vals, &dinv, &v, &yll, &zll, &z, &ep, &err, &none, &spin};
     return cuda_status(cudaLaunchCooperativeKernel((const void *)kern, grid, threads, args, smem, st));
 }
 
@@ -2565,6 +2559,8 @@ extern "C" int irk_apply_precond_noalloc(irk_ctx *c, const double *V, double *Z,
     }
     cudaStream_t st = (cudaStream_t)stream;
     int *err = reinterpret_cast<int *>(base);
+    unsigned long long *amax = reinterpret_cast<unsigned long long *>(base + 64);
+    double *scale = reinterpret_cast<double *>(base + 128);
     vec8 *vin = reinterpret_cast<vec8 *>(base + 256);
     vec8 *vout = reinterpret_cast<vec8 *>(base + 256 + na_align(N * 8));
     unsigned long long *yll = reinterpret_cast<unsigned long long *>(base + 256 + 2 * na_align(N * 8));
@@ -2573,24 +2569,25 @@ extern "C" int irk_apply_precond_noalloc(irk_ctx *c, const double *V, double *Z,
     if (cudaMemsetAsync(err, 0, 256, st) != cudaSuccess ||
         cudaMemsetAsync(yll, 0, 2 * na_align(N * 8 * w), st) != cudaSuccess)
         return IRK_ERR_CUDA;
-    const int g = grid_cap((long long)N);
-    int rc;
+    // double-float: the same power-of-two scaling as irk_apply_precond
+    const double *sc = nullptr;
+    int rc = IRK_OK;
     if (c->df) {
-        k_na_in<ArDF><<<g, 256, 0, st>>>((long long)N, c->T, c->m, c->s, V, vin);
-        rc = cuda_status(cudaGetLastError());
-        if (!rc) rc = na_sweep_prec<ArDF>(c, vin, vout, yll, zll, err, st);
-        if (!rc) k_na_out<ArDF><<<g, 256, 0, st>>>((long long)N, c->T, c->m, c->s, vout, Z);
-    } else {
-        k_na_in<ArF64><<<g, 256, 0, st>>>((long long)N, c->T, c->m, c->s, V, vin);
-        rc = cuda_status(cudaGetLastError());
-        if (!rc) rc = na_sweep_prec<ArF64>(c, vin, vout, yll, zll, err, st);
-        if (!rc) k_na_out<ArF64><<<g, 256, 0, st>>>((long long)N, c->T, c->m, c->s, vout, Z);
+        rc = launch_pow2_scale(st, (long long)N, V, amax, scale);
+        sc = scale;
     }
-    if (!rc) rc = cuda_status(cudaGetLastError());
+    if (!rc) rc = launch_to_internal_on(st, c, V, vin, sc);
+    if (!rc) rc = c->df ? na_sweep_prec<ArDF>(c, vin, vout, yll, zll, err, st)
+                        : na_sweep_prec<ArF64>(c, vin, vout, yll, zll, err, st);
+    if (!rc) rc = launch_to_external_on(st, c, vout, Z, sc);
     int herr = 0;
     if (!rc) rc = cuda_status(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
     if (!rc) rc = cuda_status(cudaStreamSynchronize(st));
-    if (!rc && (herr & IRK_DEV_ERR_TIMEOUT)) rc = IRK_ERR_TIMEOUT;
+    if (!rc) {
+        if (herr & IRK_DEV_ERR_SINGULAR) rc = IRK_ERR_SINGULAR;
+        else if (herr & IRK_DEV_ERR_NONFINITE) rc = IRK_ERR_NONFINITE;
+        else if (herr & IRK_DEV_ERR_TIMEOUT) rc = IRK_ERR_TIMEOUT;
+    }
     return rc;
 }
 
@@ -2634,7 +2631,7 @@ template <class AR, class C>
 static int sweep_group_impl(cudaStream_t st, int dev, int nitems, int b, int max_item_blocks, const int *lo,
                             const int *up, const int *rp, const int *ci, const int *voff, const void *vals,
                             const void *dinv, vec8 *vpool, unsigned long long *llpool, int ep, int *err,
-                            SweepLanes lanes) {
+                            SweepLanes lanes, int spin) {
     auto kern = k_sweep_staged<AR, C, C>;
     const size_t slot_stride = ((size_t)b * b * sizeof(C) + 127) / 128 * 128;
     int NS = std::max(1, std::min(std::min(max_item_blocks, 16), (int)((48 * 1024) / slot_stride)));
@@ -2654,7 +2651,7 @@ static int sweep_group_impl(cudaStream_t st, int dev, int nitems, int b, int max
     const vec8 *v = vpool;
     vec8 *z = vpool;
     unsigned long long *yll = llpool, *zll = llpool;
-    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &voff, &vv, &dd, &v, &yll, &zll, &z, &ep, &err, &lanes};
+    void *args[] = {&nb, &b, &NS, &lo, &up, &rp, &ci, &voff, &vv, &dd, &v, &yll, &zll, &z, &ep, &err, &lanes, &spin};
     return cuda_status(cudaLaunchCooperativeKernel((const void *)kern, grid, threads, args, smem, st));
 }
 
@@ -2665,18 +2662,18 @@ int ilu_sweep_group(cudaStream_t st, int dev, int fprec, int df, int nitems, int
                     const int *lo, const int *up, const int *rp, const int *ci, const int *voff, const void *vals,
                     const void *dinv, vec8 *vpool, unsigned long long *llpool, int ep, int *err,
                     const int *lane_of_row, const long long *vin, const long long *zout, const long long *yll,
-                    const long long *zll) {
+                    const long long *zll, int spin) {
     SweepLanes L = {lane_of_row, vin, zout, yll, zll};
     if (df) {
         if (fprec == IRK_FACTOR_FP64)
             return sweep_group_impl<ArDF, double>(st, dev, nitems, b, max_item_blocks, lo, up, rp, ci, voff, vals,
-                                                  dinv, vpool, llpool, ep, err, L);
+                                                  dinv, vpool, llpool, ep, err, L, spin);
         return sweep_group_impl<ArDF, float>(st, dev, nitems, b, max_item_blocks, lo, up, rp, ci, voff, vals, dinv,
-                                             vpool, llpool, ep, err, L);
+                                             vpool, llpool, ep, err, L, spin);
     }
     if (fprec == IRK_FACTOR_FP64)
         return sweep_group_impl<ArF64, double>(st, dev, nitems, b, max_item_blocks, lo, up, rp, ci, voff, vals, dinv,
-                                               vpool, llpool, ep, err, L);
+                                               vpool, llpool, ep, err, L, spin);
     return sweep_group_impl<ArF64, float>(st, dev, nitems, b, max_item_blocks, lo, up, rp, ci, voff, vals, dinv,
-                                          vpool, llpool, ep, err, L);
+                                          vpool, llpool, ep, err, L, spin);
 }

@@ -175,15 +175,15 @@ __device__ __forceinline__ void arnoldi_status(double *status, double est, doubl
 
 // Bounded grid-wide barrier of a cooperative launch (every CTA resident):
 // bar[0] counts the arrivals of the current generation, bar[1] is the
-// generation.  After IRK_SPIN_LIMIT polls a CTA records a timeout and the
-// barrier returns false (the caller leaves; the host resets bar per solve).
-#define IRK_GRID_SPIN_LIMIT (1 << 20)
+// generation.  After `spin` polls (irk_options.spin_limit) a CTA records a
+// timeout and the barrier returns false (the caller leaves; the host resets
+// bar per solve).
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned *p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-__device__ __forceinline__ bool grid_sync(unsigned *bar, int *err, int *s_ok) {
+__device__ __forceinline__ bool grid_sync(unsigned *bar, int *err, int *s_ok, int spin) {
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
@@ -196,7 +196,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, int *err, int *s_ok) {
         } else {
             int spins = 0;
             while (ld_acquire_u32(bar + 1) == gen) {
-                if (++spins > IRK_GRID_SPIN_LIMIT) {
+                if (++spins >= spin) {
                     ok = 0;
                     atomicOr(err, IRK_DEV_ERR_TIMEOUT);
                     break;
@@ -222,7 +222,7 @@ __device__ __forceinline__ bool grid_sync(unsigned *bar, int *err, int *s_ok) {
 template <class AR, int NT>
 __global__ void __launch_bounds__(NT) k_arnoldi(long long N, int j, int R, vec8 *w, const vec8 *V, Scal *slots,
                                                  double *H, double *cs, double *sn, double *g, double *est,
-                                                 vec8 *part, unsigned *bar, int *err, double *status) {
+                                                 vec8 *part, unsigned *bar, int *err, double *status, int spin) {
     typedef typename AR::val val;
     __shared__ val sh[32];
     __shared__ int s_ok;
@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(NT) k_arnoldi(long long N, int j, int R, vec8 
         vec8 *pb = part + (i & 1) * gridDim.x;
         const val r = block_reduce<AR>(AR::value(acc), sh);
         if (threadIdx.x == 0) AR::st(pb + blockIdx.x, r);
-        if (!grid_sync(bar, err, &s_ok)) {
+        if (!grid_sync(bar, err, &s_ok, spin)) {
             if (blockIdx.x == 0 && threadIdx.x == 0) arnoldi_status(status, 0.0, 0.0, err);
             return;
         }
@@ -398,7 +398,7 @@ template <class AR>
 __global__ void __launch_bounds__(1024) k_arnoldi_smem(long long N, long long chunk, int j, int R, vec8 *w,
                                                        const vec8 *V, Scal *slots, double *H, double *cs,
                                                        double *sn, double *g, double *est, vec8 *part,
-                                                       unsigned *bar, int *err, double *status) {
+                                                       unsigned *bar, int *err, double *status, int spin) {
     typedef typename AR::val val;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     vec8 *ws = reinterpret_cast<vec8 *>(smem_raw);
@@ -443,7 +443,7 @@ __global__ void __launch_bounds__(1024) k_arnoldi_smem(long long N, long long ch
         vec8 *pb = part + (i & 1) * gridDim.x;
         const val r = block_reduce<AR>(AR::value(acc), sh);
         if (threadIdx.x == 0) AR::st(pb + blockIdx.x, r);
-        if (!grid_sync(bar, err, &s_ok)) {
+        if (!grid_sync(bar, err, &s_ok, spin)) {
             if (blockIdx.x == 0 && threadIdx.x == 0) arnoldi_status(status, 0.0, 0.0, err);
             return;
         }
@@ -545,8 +545,9 @@ static bool launch_arnoldi_smem(irk_ctx *c, int j, int restart, vec8 *w, int *rc
     double *est = &scal(c, 1)->d;
     vec8 *part = reinterpret_cast<vec8 *>(c->d_part);
     double *status = irk_status_ptr(c);
+    int spin = c->spin;
     void *args[] = {&N, &chunk, &jj, &R, &w, &V, &slots, &c->d_H, &c->d_cs, &c->d_sn, &c->d_g, &est, &part,
-                    &c->d_gbar, &c->d_err, &status};
+                    &c->d_gbar, &c->d_err, &status, &spin};
     *rc = cuda_status(cudaLaunchCooperativeKernel(fn, sms, 1024, args, smem, c->stream));
     c->launches++;
     return true;
@@ -564,8 +565,9 @@ int launch_arnoldi(irk_ctx *c, int j, int restart, vec8 *w) {
     double *est = &scal(c, 1)->d;
     vec8 *part = reinterpret_cast<vec8 *>(c->d_part);
     double *status = irk_status_ptr(c);
+    int spin = c->spin;
     void *args[] = {&N, &jj, &R, &w, &V, &slots, &c->d_H, &c->d_cs, &c->d_sn, &c->d_g, &est, &part, &c->d_gbar,
-                    &c->d_err, &status};
+                    &c->d_err, &status, &spin};
     const void *fn;
     if (c->df)
         fn = sh.threads == 256 ? (const void *)k_arnoldi<ArDF, 256> : (const void *)k_arnoldi<ArDF, 1024>;

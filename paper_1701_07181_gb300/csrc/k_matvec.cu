@@ -559,38 +559,101 @@ __global__ void __launch_bounds__(256) k_matvec_pipe(MatvecParams P, int G, int 
 }
 
 template <class AR>
-__global__ void k_to_internal(long long N, int T, int m, int s, const double *__restrict__ src, vec8 *dst) {
-    // dst[(i*s + k)*m + a] = src[(k*T + i)*m + a]
+__global__ void k_to_internal(long long N, int T, int m, int s, const double *__restrict__ src, vec8 *dst,
+                              const double *__restrict__ scale) {
+    // dst[(i*s + k)*m + a] = src[(k*T + i)*m + a] * scale[0]
+    const double f = scale ? scale[0] : 1.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
         long long a = e % m;
         long long r = e / m;
         long long k = r % s;
         long long i = r / s;
-        AR::st(dst + e, AR::from_double(src[(k * T + i) * m + a]));
+        AR::st(dst + e, AR::from_double(src[(k * T + i) * m + a] * f));
     }
 }
 
 template <class AR>
-__global__ void k_to_external(long long N, int T, int m, int s, const vec8 *__restrict__ src, double *dst) {
+__global__ void k_to_external(long long N, int T, int m, int s, const vec8 *__restrict__ src, double *dst,
+                              const double *__restrict__ scale) {
+    const double f = scale ? scale[1] : 1.0;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < N; e += (long long)gridDim.x * blockDim.x) {
         long long a = e % m;
         long long r = e / m;
         long long k = r % s;
         long long i = r / s;
-        dst[(k * T + i) * m + a] = AR::to_double(AR::ld(src + e));
+        dst[(k * T + i) * m + a] = AR::to_double(AR::ld(src + e)) * f;
     }
 }
 
+// Largest |x| of a warp's values as binary64 bits (non-negative doubles order
+// like their bit patterns), merged into *amax by one atomic per warp.
+__device__ __forceinline__ void warp_amax(unsigned long long bits, unsigned long long *amax) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, bits, d);
+        bits = o > bits ? o : bits;
+    }
+    if ((threadIdx.x & 31) == 0 && bits) atomicMax(amax, bits);
+}
+
 template <class AR>
-__global__ void k_convert_blocks(long long total, int m, const double *__restrict__ src, vec8 *dst) {
-    // row-major source block element (a, c) -> column-major destination
+__global__ void k_convert_blocks(long long total, int m, const double *__restrict__ src, vec8 *dst,
+                                 unsigned long long *amax, int *err) {
+    // row-major source block element (a, c) -> column-major destination;
+    // the loop runs a whole number of warp-wide rounds so that every lane
+    // takes part in the warp's maximum
     const long long mm = (long long)m * m;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total; e += (long long)gridDim.x * blockDim.x) {
-        long long blk = e / mm;
-        long long r = e - blk * mm;
-        long long c = r / m, a = r - c * m;
-        AR::st(dst + e, AR::from_double(src[blk * mm + a * m + c]));
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    unsigned long long big = 0;
+    bool bad = false;
+    for (long long e0 = start - (threadIdx.x & 31); e0 < total; e0 += stride) {
+        const long long e = e0 + (threadIdx.x & 31);
+        if (e < total) {
+            long long blk = e / mm;
+            long long r = e - blk * mm;
+            long long c = r / m, a = r - c * m;
+            const double v = src[blk * mm + a * m + c];
+            AR::st(dst + e, AR::from_double(v));
+            if (!isfinite(v)) {
+                bad = true;
+            } else {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(fabs(v));
+                big = b > big ? b : big;
+            }
+        }
     }
+    warp_amax(big, amax);
+    if (bad) atomicOr(err, IRK_DEV_ERR_NONFINITE);
+}
+
+// Largest |src[q]| over n values into *amax (zeroed by the caller).
+__global__ void k_amax(long long n, const double *__restrict__ src, unsigned long long *amax) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    unsigned long long big = 0;
+    for (long long e0 = blockIdx.x * (long long)blockDim.x + threadIdx.x - (threadIdx.x & 31); e0 < n; e0 += stride) {
+        const long long e = e0 + (threadIdx.x & 31);
+        if (e < n) {
+            const double v = fabs(src[e]);
+            if (isfinite(v)) {
+                const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+                big = b > big ? b : big;
+            }
+        }
+    }
+    warp_amax(big, amax);
+}
+
+// (2^-e, 2^e) with 2^e <= amax < 2^(e+1); (1, 1) for zero.  Built from the
+// exponent bits, so both factors are exact powers of two.
+__global__ void k_pow2_pair(const unsigned long long *amax, double *scale) {
+    const unsigned long long b = *amax;
+    int e = (int)((b >> 52) & 0x7ff) - 1023;  // subnormal maxima count as 2^-1023
+    if (b == 0) e = 0;
+    if (e < -1000) e = -1000;
+    if (e > 1000) e = 1000;
+    scale[0] = ldexp(1.0, -e);
+    scale[1] = ldexp(1.0, e);
 }
 
 int grid_for(long long work, int threads) {
@@ -903,33 +966,49 @@ int launch_jacobian(irk_ctx *c, const vec8 *x, vec8 *y) {
     return cuda_status(cudaGetLastError());
 }
 
-int launch_to_internal(irk_ctx *c, const double *src, vec8 *dst) {
+int launch_to_internal_on(cudaStream_t st, const irk_ctx *c, const double *src, vec8 *dst, const double *scale) {
     int g = grid_for(c->N, 256);
     if (c->df)
-        k_to_internal<ArDF><<<g, 256, 0, c->stream>>>(c->N, c->T, c->m, c->s, src, dst);
+        k_to_internal<ArDF><<<g, 256, 0, st>>>(c->N, c->T, c->m, c->s, src, dst, scale);
     else
-        k_to_internal<ArF64><<<g, 256, 0, c->stream>>>(c->N, c->T, c->m, c->s, src, dst);
-    c->launches++;
+        k_to_internal<ArF64><<<g, 256, 0, st>>>(c->N, c->T, c->m, c->s, src, dst, scale);
     return cuda_status(cudaGetLastError());
 }
 
-int launch_to_external(irk_ctx *c, const vec8 *src, double *dst) {
+int launch_to_external_on(cudaStream_t st, const irk_ctx *c, const vec8 *src, double *dst, const double *scale) {
     int g = grid_for(c->N, 256);
     if (c->df)
-        k_to_external<ArDF><<<g, 256, 0, c->stream>>>(c->N, c->T, c->m, c->s, src, dst);
+        k_to_external<ArDF><<<g, 256, 0, st>>>(c->N, c->T, c->m, c->s, src, dst, scale);
     else
-        k_to_external<ArF64><<<g, 256, 0, c->stream>>>(c->N, c->T, c->m, c->s, src, dst);
-    c->launches++;
+        k_to_external<ArF64><<<g, 256, 0, st>>>(c->N, c->T, c->m, c->s, src, dst, scale);
     return cuda_status(cudaGetLastError());
 }
 
-int launch_convert_blocks(irk_ctx *c, const double *src, vec8 *dst, long long nblocks) {
+int launch_to_internal(irk_ctx *c, const double *src, vec8 *dst, const double *scale) {
+    c->launches++;
+    return launch_to_internal_on(c->stream, c, src, dst, scale);
+}
+
+int launch_to_external(irk_ctx *c, const vec8 *src, double *dst, const double *scale) {
+    c->launches++;
+    return launch_to_external_on(c->stream, c, src, dst, scale);
+}
+
+int launch_pow2_scale(cudaStream_t st, long long n, const double *src, unsigned long long *amax, double *scale) {
+    if (cudaMemsetAsync(amax, 0, sizeof(unsigned long long), st) != cudaSuccess) return IRK_ERR_CUDA;
+    k_amax<<<grid_for(n, 256), 256, 0, st>>>(n, src, amax);
+    k_pow2_pair<<<1, 1, 0, st>>>(amax, scale);
+    return cuda_status(cudaGetLastError());
+}
+
+int launch_convert_blocks(irk_ctx *c, const double *src, vec8 *dst, long long nblocks, unsigned long long *amax,
+                          int *err) {
     long long total = nblocks * c->m * c->m;
     int g = grid_for(total, 256);
     if (c->df)
-        k_convert_blocks<ArDF><<<g, 256, 0, c->stream>>>(total, c->m, src, dst);
+        k_convert_blocks<ArDF><<<g, 256, 0, c->stream>>>(total, c->m, src, dst, amax, err);
     else
-        k_convert_blocks<ArF64><<<g, 256, 0, c->stream>>>(total, c->m, src, dst);
+        k_convert_blocks<ArF64><<<g, 256, 0, c->stream>>>(total, c->m, src, dst, amax, err);
     c->launches++;
     return cuda_status(cudaGetLastError());
 }

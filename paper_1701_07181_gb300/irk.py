@@ -40,7 +40,8 @@ class Options(ctypes.Structure):
                 ("formulation", ctypes.c_int), ("shift", ctypes.POINTER(ctypes.c_double)),
                 ("stream", ctypes.c_void_p), ("timing", ctypes.c_int), ("sweep", ctypes.c_int),
                 ("ordering", ctypes.c_int), ("partitions", ctypes.c_int),
-                ("partition", ctypes.POINTER(ctypes.c_int32)), ("stage_jacobians", ctypes.c_int)]
+                ("partition", ctypes.POINTER(ctypes.c_int32)), ("stage_jacobians", ctypes.c_int),
+                ("spin_limit", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -61,7 +62,7 @@ EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor"
            "irk_strerror", "irk_apply_precond_noalloc", "irk_group_create", "irk_group_submit",
            "irk_group_step", "irk_group_query", "irk_group_collect", "irk_group_device_bytes",
            "irk_group_destroy", "irk_dirk_setup", "irk_dirk_step", "irk_dirk_destroy", "irk_set_timing",
-           "irk_step_outputs"]
+           "irk_step_outputs", "irk_set_spin_limit"]
 
 
 def load():
@@ -85,6 +86,7 @@ def load():
         lib.irk_apply_precond.argtypes = [P, P, P, I]
         lib.irk_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
         lib.irk_set_timing.argtypes = [P, I]
+        lib.irk_set_spin_limit.argtypes = [P, I]
         lib.irk_step_outputs.argtypes = [P, P, P, P, D, P, P, I]
         lib.irk_destroy.argtypes = [P]
         lib.irk_destroy.restype = None
@@ -136,7 +138,7 @@ class Solver:
     def __init__(self, s, T, m, row_ptr, col_idx, J, M, A=None, precond="uncoupled",
                  factor_prec="fp64", krylov="fp64", formulation="transformed", restart=30,
                  max_iter=3000, shift=None, stream=None, timing=False, sweep="auto",
-                 ordering="natural", partitions=0, partition=None, stage_jacobians=False):
+                 ordering="natural", partitions=0, partition=None, stage_jacobians=False, spin_limit=0):
         lib = load()
         self._lib = lib
         self.s, self.T, self.m = int(s), int(T), int(m)
@@ -160,6 +162,7 @@ class Solver:
         opt.ordering = {"natural": 0, "multicolor": 1}[ordering]
         opt.partitions = int(partitions)
         opt.stage_jacobians = 1 if stage_jacobians else 0
+        opt.spin_limit = int(spin_limit)
         self._part = None
         if partition is not None:
             self._part = np.ascontiguousarray(partition, dtype=np.int32)
@@ -252,6 +255,11 @@ class Solver:
         bb = None if b is None else (ctypes.c_double * self.s)(*[float(x) for x in b])
         self._check(self._lib.irk_step_outputs(self._h, Wp, bb, u0p, float(dt), Kp, u1p, sp), "irk_step_outputs")
         return K, u1
+
+    def set_spin_limit(self, spin_limit):
+        """irk_set_spin_limit: polls of a device wait on another thread block
+        before it gives up (0 = the default)."""
+        self._check(self._lib.irk_set_spin_limit(self._h, int(spin_limit)), "irk_set_spin_limit")
 
     def set_timing(self, timing):
         """irk_set_timing: 0, 1 or 2 (see irk_options.timing) for the calls that follow."""

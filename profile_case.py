@@ -8,13 +8,17 @@ m = 40, s = 3: inputs still larger than L2) with the benchmark's options
 (FP32 factors, double-float Krylov vectors, two-colour ordering), so DRAM
 counters per launch can be scaled to the full workload by the element count.
 
-Usage: ``python -m paper_1701_07181_gb300.profile_case [--nx 60 --ny 60 --m 40 --s 3 --solves 2]``
+Usage: ``python profile_case.py [--nx 60 --ny 60 --m 40 --s 3 --solves 2]``
 """
 from __future__ import annotations
 
 import argparse
+import os
+import sys
 
 import numpy as np
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main(argv=None):
@@ -28,7 +32,7 @@ def main(argv=None):
     args = ap.parse_args(argv)
     import torch
 
-    from . import inputs, irk
+    from paper_1701_07181_gb300 import inputs, irk
     P = inputs.make_problem(inputs.mesh_2d_periodic(args.nx, args.ny), args.m, args.s, 0.1, 6.0, seed=0)
 
     def dev(a):

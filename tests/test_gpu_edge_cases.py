@@ -18,6 +18,7 @@ import pytest
 
 import oracle
 from paper_1701_07181_gb300 import inputs
+from _parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -26,10 +27,6 @@ torch = pytest.importorskip("torch")
 def _irk():
     from paper_1701_07181_gb300 import irk
     return irk
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - b) / np.linalg.norm(b))
 
 
 def check(P, ordering="natural", sweep="auto", expect_two_colour=None, fp64_factors=True):

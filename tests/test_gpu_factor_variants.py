@@ -15,6 +15,7 @@ import oracle
 from paper_1701_07181_gb300 import inputs
 
 from test_oracle_ordering import greedy_colouring_order
+from _parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -23,10 +24,6 @@ torch = pytest.importorskip("torch")
 def _irk():
     from paper_1701_07181_gb300 import irk
     return irk
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 @pytest.mark.parametrize("m", [12, 20, 24, 40, 50])

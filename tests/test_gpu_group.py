@@ -14,6 +14,7 @@ import pytest
 
 import oracle
 from paper_1701_07181_gb300 import inputs
+from _parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -26,10 +27,6 @@ def _irk():
 
 def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a)).cuda()
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def make(nx, ny, m=12, s=3, seed=0, dt=0.2):

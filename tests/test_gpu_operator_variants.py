@@ -17,6 +17,7 @@ import pytest
 
 import oracle
 from paper_1701_07181_gb300 import inputs
+from _parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -26,10 +27,6 @@ N_VARIANTS = 11
 
 def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a)).cuda()
-
-
-def rel(a, b):
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def make(kind, s, m, seed=3):

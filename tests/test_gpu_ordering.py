@@ -8,6 +8,7 @@ import oracle
 from paper_1701_07181_gb300 import inputs
 
 from test_oracle_ordering import greedy_colouring_order, strip_partitions
+from _parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -15,11 +16,6 @@ torch = pytest.importorskip("torch")
 
 def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a)).cuda()
-
-
-def rel(a, b):
-    a = a.cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def setup(mesh="2d", m=12, s=3, seed=21):

@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 from paper_1701_07181_gb300 import inputs
+from _parity import rel
 
 pytestmark = pytest.mark.gpu
 
@@ -28,11 +29,6 @@ def _irk():
 
 def dev(a):
     return torch.as_tensor(np.ascontiguousarray(a)).cuda()
-
-
-def rel(a, b):
-    a = a.cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def problem(kind, s, m=None, seed=11, dt=0.1, sigma=4.0):

@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 from paper_1701_07181_gb300 import inputs
+from _parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -23,11 +24,6 @@ torch = pytest.importorskip("torch")
 def _irk():
     from paper_1701_07181_gb300 import irk
     return irk
-
-
-def rel(a, b):
-    a = a.cpu().numpy() if hasattr(a, "cpu") else np.asarray(a)
-    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
 def problem(s, m=12, seed=7, kind="2d"):

@@ -11,13 +11,10 @@ import pytest
 
 from oracle import dirk, tableau
 from paper_1701_07181_gb300 import inputs
+from _parity import rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
-
-
-def rel(a, b):
-    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.mark.parametrize("s", [2, 3])
