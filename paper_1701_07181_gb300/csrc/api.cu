@@ -682,6 +682,9 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     bnorm = *beta_h;
     if (!rc && !std::isfinite(bnorm)) rc = IRK_ERR_NONFINITE;
     bool x_zero = true;
+    // binary32 factors write binary32-valued z_j = P^{-1} v_j (double-float
+    // with zero low words): their operator products skip those words
+    const int z_f32 = c->df && c->pc.kind != IRK_PC_NONE && c->fprec != IRK_FACTOR_FP64;
     while (rc == IRK_OK && bnorm > 0.0) {
         vec8 *V0 = c->d_V;
         if (x_zero) {
@@ -717,7 +720,7 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
             if ((rc = pc_apply(c, Vj, Zj))) break;
             tmark_end(c, tm, 1);
             tm = tmark_begin(c);
-            if ((rc = launch_matvec(c, Zj, w, nullptr, dt, 0))) break;
+            if ((rc = launch_matvec(c, Zj, w, nullptr, dt, 0, z_f32))) break;
             tmark_end(c, tm, 0);
             tm = tmark_begin(c);
             rc = launch_arnoldi(c, j, Rs, w);

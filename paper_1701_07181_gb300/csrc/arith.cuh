@@ -14,6 +14,7 @@ struct ArF64 {
     static __device__ __forceinline__ void st(vec8 *p, val v) { *reinterpret_cast<double *>(p) = v; }
     static __device__ __forceinline__ acc zero() { return 0.0; }
     static __device__ __forceinline__ void fma(acc &a, val x, val y) { a = ::fma(x, y, a); }
+    static __device__ __forceinline__ void renorm(acc &) {}
     static __device__ __forceinline__ void add_to(acc &a, val x) { a += x; }
     static __device__ __forceinline__ val value(acc a) { return a; }
     static __device__ __forceinline__ val add(val a, val b) { return a + b; }
@@ -46,6 +47,9 @@ struct ArDF {
     }
     static __device__ __forceinline__ acc zero() { return df_acc_zero(); }
     static __device__ __forceinline__ void fma(acc &a, val x, val y) { df_acc_fma(a, x, y); }
+    // fold the error term into the sum; the operator product does it after
+    // every eighth column of a block and after its last column
+    static __device__ __forceinline__ void renorm(acc &a) { df_acc_renorm(a); }
     static __device__ __forceinline__ void add_to(acc &a, val x) { df_acc_add(a, x); }
     static __device__ __forceinline__ val value(acc a) { return df_acc_value(a); }
     static __device__ __forceinline__ val add(val a, val b) { return df_add(a, b); }

@@ -104,6 +104,31 @@ __device__ __forceinline__ void df_acc_fma(df_acc &acc, df64 x, df64 y) {
     acc.c = __fadd_rn(c, __fadd_rn(t, e));
 }
 
+// acc += x * y for a binary32 y (a double-word value whose low word is 0):
+// the same operations as df_acc_fma with the x.hi * y.lo term, which is
+// exactly zero, left out.
+__device__ __forceinline__ void df_acc_fma_f(df_acc &acc, df64 x, float y) {
+    float p = __fmul_rn(x.hi, y);
+    float e = __fmaf_rn(x.hi, y, -p);
+    float s, t;
+    two_sum(acc.s, p, s, t);
+    float c = __fmaf_rn(x.lo, y, acc.c);
+    acc.s = s;
+    acc.c = __fadd_rn(c, __fadd_rn(t, e));
+}
+
+// Fold the error term into the running sum (s, c) <- FastTwoSum(s, c), so that
+// c holds only what s cannot: without it c grows with every term and its own
+// rounding errors (u |c| per addition, u = 2^-24) build up to about
+// K u^2 |sum| over K terms; folding every few terms keeps |c| <= ulp(s) and the
+// error near sqrt(K) u^2.  When |s| < |c| the fold is still within u min(|s|, |c|).
+__device__ __forceinline__ void df_acc_renorm(df_acc &acc) {
+    float s, c;
+    fast_two_sum(acc.s, acc.c, s, c);
+    acc.s = s;
+    acc.c = c;
+}
+
 // acc += x (a double-word value)
 __device__ __forceinline__ void df_acc_add(df_acc &acc, df64 x) {
     float s, t;

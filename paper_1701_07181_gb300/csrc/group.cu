@@ -117,9 +117,16 @@ __device__ __forceinline__ void g_accum(typename AR::acc (&dst)[S], const vec8 *
 #pragma unroll
             for (int u = 0; u < CH; ++u) xv[l][u] = (c0 + u < m) ? AR::ld(x + l * m + c0 + u) : AR::from_float(0.f);
 #pragma unroll
-        for (int u = 0; u < CH; ++u)
+        for (int u = 0; u < CH; ++u) {
 #pragma unroll
             for (int l = 0; l < S; ++l) AR::fma(dst[l], bv[u], xv[l][u]);
+            // the single-request product's fold points: after every eighth
+            // column of a block and after its last column
+            const int c = c0 + u;
+            if (c < m && ((c & 7) == 7 || c == m - 1))
+#pragma unroll
+                for (int l = 0; l < S; ++l) AR::renorm(dst[l]);
+        }
     }
 }
 

@@ -135,8 +135,10 @@ struct irk_ctx {
 };
 
 // ---- launchers (k_matvec.cu) ----
-// y = B x (mode 0) or y = rhs - B x (mode 1); form: IRK_TRANSFORMED / UNTRANSFORMED
-int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt, int mode);
+// y = B x (mode 0) or y = rhs - B x (mode 1); form: IRK_TRANSFORMED / UNTRANSFORMED;
+// x_f32: every value of x is binary32 (a preconditioned vector from binary32
+// factors), which lets the double-float kernel skip the low-word products
+int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt, int mode, int x_f32 = 0);
 // y = (I (x) J) x in the context's arithmetic (internal layout)
 int launch_jacobian(irk_ctx *c, const vec8 *x, vec8 *y);
 // operator-product form value for the Jacobian alone (internal; beside the

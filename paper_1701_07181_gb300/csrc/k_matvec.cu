@@ -31,6 +31,7 @@ namespace {
 
 struct MatvecParams {
     int T, m, form, mode;
+    int xf32;  // 1: every x value is binary32 (double-float with a zero low word)
     const int *rp, *ci;
     const vec8 *J, *M, *x, *rhs;
     vec8 *y;
@@ -41,6 +42,12 @@ struct MatvecParams {
     long long jstride;
     KCoef Acomb[IRK_MAX_S * IRK_MAX_S];
 };
+
+// Columns after which every double-float accumulator of the operator product
+// folds its error term into its sum (df_acc_renorm): every eighth column of a
+// block and its last one.  All launch variants fold at the same columns, so
+// they stay bitwise identical.
+__device__ __forceinline__ bool fold_after(int c, int m) { return (c & 7) == 7 || c == m - 1; }
 
 // dst[l] += sum_c B[c][a] x[l][c] for one column-major block (thread's row a
 // pre-applied to B).  Chunks of CH columns: all loads of a chunk are issued
@@ -57,9 +64,13 @@ __device__ __forceinline__ void accum_block(typename AR::acc (&dst)[S], const ve
 #pragma unroll
             for (int u = 0; u < CH; ++u) xv[l][u] = (c0 + u < m) ? AR::ld(x + l * m + c0 + u) : AR::from_float(0.f);
 #pragma unroll
-        for (int u = 0; u < CH; ++u)
+        for (int u = 0; u < CH; ++u) {
 #pragma unroll
             for (int l = 0; l < S; ++l) AR::fma(dst[l], bv[u], xv[l][u]);
+            if (c0 + u < m && fold_after(c0 + u, m))
+#pragma unroll
+                for (int l = 0; l < S; ++l) AR::renorm(dst[l]);
+        }
     }
 }
 
@@ -160,51 +171,93 @@ __device__ __forceinline__ void accum_block_b(df_acc (&dst)[S], const vec8 *Bp, 
                 }
 #pragma unroll
         for (int u = 0; u < CH; ++u)
-            if (c0 + u < B)
+            if (c0 + u < B) {
 #pragma unroll
                 for (int l = 0; l < S; ++l) ArDF::fma(dst[l], bv[u], xv[l][u]);
+                if (fold_after(c0 + u, B))
+#pragma unroll
+                    for (int l = 0; l < S; ++l) ArDF::renorm(dst[l]);
+            }
     }
 }
+
+// A block entry streamed from HBM: read once, so it skips L1 (no_allocate)
+// and leaves L1 to the neighbours' stage values, which every thread of a
+// group reads and which would otherwise be evicted by the block stream.
+__device__ __forceinline__ df64 ld_stream(const vec8 *p) {
+    float h, l;
+    asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(h), "=f"(l) : "l"(p));
+    return df_make(h, l);
+}
+
+// Element rows per CTA of the look-ahead kernel: as many as fill whole warps
+// (G B a multiple of 32) within 256 threads, else 256 / B.
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
+__host__ __device__ constexpr int sp_groups(int B) {
+    return (B * 32 / gcd_c(B, 32) <= 256) ? (256 / (B * 32 / gcd_c(B, 32))) * (32 / gcd_c(B, 32)) : 256 / B;
+}
+__host__ __device__ constexpr int sp_threads(int B) { return (sp_groups(B) * B + 31) / 32 * 32; }
 
 // accum_block_b with the block loads one chunk ahead: chunk c + CH's
 // columns are requested before chunk c's arithmetic, so the loads overlap a
 // chunk of work instead of stalling right before it.  Same operation order.
 // (Reaching across into the next block's first chunk as well costs
 // registers, hence occupancy, and measured slower: 0.30 -> 0.35 ms.)
-template <int S, int B, int CH>
+// XF: the x values are binary32 (zero low words, e.g. a preconditioned
+// vector from binary32 factors): the x.hi * y.lo term, exactly zero, is left
+// out of every multiply-add (df_acc_fma_f), with the same result.
+template <int S, int B, int CH, bool XF>
 __device__ __forceinline__ void accum_block_sp(df_acc (&dst)[S], const vec8 *Bp, const vec8 *x) {
     df64 cur[CH], nxt[CH];
 #pragma unroll
     for (int u = 0; u < CH; ++u)
-        if (u < B) cur[u] = ArDF::ld(Bp + u * B);
+        if (u < B) cur[u] = ld_stream(Bp + u * B);
 #pragma unroll
     for (int c0 = 0; c0 < B; c0 += CH) {
 #pragma unroll
         for (int u = 0; u < CH; ++u)
-            if (c0 + CH + u < B) nxt[u] = ArDF::ld(Bp + (c0 + CH + u) * B);
+            if (c0 + CH + u < B) nxt[u] = ld_stream(Bp + (c0 + CH + u) * B);
         df64 xv[S][CH];
+        float xf[S][CH];
 #pragma unroll
         for (int l = 0; l < S; ++l)
 #pragma unroll
             for (int u = 0; u < CH; u += 2)
                 if (c0 + u < B) {
                     const float4 f = __ldg(reinterpret_cast<const float4 *>(x + l * B + c0 + u));
-                    xv[l][u] = df_make(f.x, f.y);
-                    xv[l][u + 1] = df_make(f.z, f.w);
+                    if (XF) {
+                        xf[l][u] = f.x;
+                        xf[l][u + 1] = f.z;
+                    } else {
+                        xv[l][u] = df_make(f.x, f.y);
+                        xv[l][u + 1] = df_make(f.z, f.w);
+                    }
                 }
 #pragma unroll
         for (int u = 0; u < CH; ++u)
-            if (c0 + u < B)
+            if (c0 + u < B) {
 #pragma unroll
-                for (int l = 0; l < S; ++l) ArDF::fma(dst[l], cur[u], xv[l][u]);
+                for (int l = 0; l < S; ++l) {
+                    if (XF)
+                        df_acc_fma_f(dst[l], cur[u], xf[l][u]);
+                    else
+                        ArDF::fma(dst[l], cur[u], xv[l][u]);
+                }
+                if (fold_after(c0 + u, B))
+#pragma unroll
+                    for (int l = 0; l < S; ++l) ArDF::renorm(dst[l]);
+            }
 #pragma unroll
         for (int u = 0; u < CH; ++u) cur[u] = nxt[u];
     }
 }
 
-template <int S, int B, int CH>
-__global__ void __launch_bounds__(256) k_matvec_sp(MatvecParams P) {
-    constexpr int G = 256 / B;
+// Launch bounds: 32 registers (64 resident warps) for binary32 inputs and up
+// to three stages, 40 for double-float inputs; four stages unconstrained.
+template <int S, int B, int CH, bool XF>
+__global__ void __launch_bounds__(sp_threads(B), S <= 3 ? (XF ? 2048 : 1536) / sp_threads(B) : 1)
+    k_matvec_sp(MatvecParams P) {
+    constexpr int G = sp_groups(B);
     constexpr long long BB = (long long)B * B, SB = (long long)S * B;
     const int g = threadIdx.x / B;
     const int a = threadIdx.x - g * B;
@@ -217,14 +270,14 @@ __global__ void __launch_bounds__(256) k_matvec_sp(MatvecParams P) {
             z[l] = ArDF::zero();
         }
         const int p0 = P.rp[i], p1 = P.rp[i + 1];
-        for (int p = p0; p < p1; ++p) accum_block_sp<S, B, CH>(t, P.J + p * BB + a, P.x + P.ci[p] * SB);
-        if (P.form != IRK_FORM_JACOBIAN) accum_block_sp<S, B, CH>(z, P.M + i * BB + a, P.x + i * SB);
+        for (int p = p0; p < p1; ++p) accum_block_sp<S, B, CH, XF>(t, P.J + p * BB + a, P.x + P.ci[p] * SB);
+        if (P.form != IRK_FORM_JACOBIAN) accum_block_sp<S, B, CH, XF>(z, P.M + i * BB + a, P.x + i * SB);
         store_row<ArDF, S>(P, i, a, t, z);
     }
 }
 
 template <int S, int B, int CH>
-__global__ void __launch_bounds__(256) k_matvec_b(MatvecParams P) {
+__global__ void __launch_bounds__(256, S <= 3 ? 6 : 1) k_matvec_b(MatvecParams P) {
     constexpr int G = 256 / B;
     constexpr long long BB = (long long)B * B, SB = (long long)S * B;
     const int g = threadIdx.x / B;
@@ -276,11 +329,17 @@ __device__ __forceinline__ void accum_block_rb(df_acc (&dst)[2 * H][S], const ve
                 }
 #pragma unroll
         for (int u = 0; u < CH; ++u)
-            if (c0 + u < B)
+            if (c0 + u < B) {
 #pragma unroll
                 for (int r = 0; r < 2 * H; ++r)
 #pragma unroll
                     for (int l = 0; l < S; ++l) ArDF::fma(dst[r][l], bv[u][r], xv[l][u]);
+                if (fold_after(c0 + u, B))
+#pragma unroll
+                    for (int r = 0; r < 2 * H; ++r)
+#pragma unroll
+                        for (int l = 0; l < S; ++l) ArDF::renorm(dst[r][l]);
+            }
     }
 }
 
@@ -357,6 +416,7 @@ __global__ void __launch_bounds__(256) k_matvec_ps(MatvecParams P, int untransfo
                         q = AR::value(qa);
                     }
                     AR::fma(t[kk], AR::ld(Jp + kk * P.jstride + (long long)c * m), q);
+                    if (fold_after(c, m)) AR::renorm(t[kk]);
                 }
             }
         }
@@ -404,14 +464,21 @@ __device__ __forceinline__ void accum_block_smem(typename AR::acc (&dst)[S], con
 #pragma unroll
             for (int u = 0; u < U; ++u) xv[l][u] = lds<AR>(x + l * m + c + u);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+        for (int u = 0; u < U; ++u) {
 #pragma unroll
             for (int l = 0; l < S; ++l) AR::fma(dst[l], bv[u], xv[l][u]);
+            if (fold_after(c + u, m))
+#pragma unroll
+                for (int l = 0; l < S; ++l) AR::renorm(dst[l]);
+        }
     }
     for (; c < m; ++c) {
         const val b = lds<AR>(B + c * m);
 #pragma unroll
         for (int l = 0; l < S; ++l) AR::fma(dst[l], b, lds<AR>(x + l * m + c));
+        if (fold_after(c, m))
+#pragma unroll
+            for (int l = 0; l < S; ++l) AR::renorm(dst[l]);
     }
 }
 
@@ -758,9 +825,12 @@ bool run_matvec_rb(const MatvecParams &P, cudaStream_t st) {
 template <int S, int B>
 bool run_matvec_sp(const MatvecParams &P, cudaStream_t st) {
     if (P.m != B) return false;
-    constexpr int G = 256 / B;
+    constexpr int G = sp_groups(B);
     const long long g = (P.T + G - 1) / G;
-    k_matvec_sp<S, B, 4><<<(int)g, (G * B + 31) / 32 * 32, 0, st>>>(P);
+    if (P.xf32)
+        k_matvec_sp<S, B, 4, true><<<(int)g, sp_threads(B), 0, st>>>(P);
+    else
+        k_matvec_sp<S, B, 4, false><<<(int)g, sp_threads(B), 0, st>>>(P);
     return true;
 }
 
@@ -771,7 +841,9 @@ bool run_matvec_fixed(const MatvecParams &P, int form, cudaStream_t st) {
         if (form == 2)
             return run_matvec_rb<S, 40, 2>(P, st) || run_matvec_rb<S, 50, 1>(P, st) ||
                    run_matvec_rb<S, 24, 2>(P, st) || run_matvec_rb<S, 20, 2>(P, st) || run_matvec_rb<S, 12, 2>(P, st);
-        if (form == 4)
+        // binary32 inputs: the look-ahead form's binary32-input kernel stands in
+        // for every compile-time form (all of them give the same result)
+        if (form == 4 || (P.xf32 && (form == 1 || form == 3)))
             return run_matvec_sp<S, 40>(P, st) || run_matvec_sp<S, 50>(P, st) || run_matvec_sp<S, 24>(P, st) ||
                    run_matvec_sp<S, 20>(P, st) || run_matvec_sp<S, 12>(P, st);
         if (form == 3)
@@ -914,13 +986,14 @@ int launch_matvec_ps(irk_ctx *c, MatvecParams P) {
 // chosen variant of a context's class (-1 before the first product)
 int matvec_variant(const irk_ctx *c) { return c->mv_variant; }
 
-int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt, int mode) {
+int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt, int mode, int x_f32) {
     MatvecParams P;
     memset(&P, 0, sizeof(P));
     P.T = c->T;
     P.m = c->m;
     P.form = c->opt.formulation;
     P.mode = mode;
+    P.xf32 = (x_f32 && c->df) ? 1 : 0;
     P.rp = c->d_rp;
     P.ci = c->d_ci;
     P.J = c->d_J;
