@@ -417,8 +417,11 @@ typedef struct {
      * s = 2..4, m = 12, 20, 24, 40 or 50; else variant 0's launch), 8 the
      * same register-blocked (four rows per thread, two for m = 50), 9 as 7
      * with eight columns of loads in flight per thread, 10 as 7 with the
-     * block loads issued one chunk ahead; -1 before the first product.  The
-     * environment variable IRK_MATVEC_VARIANT=<0..10>, read when
+     * block loads issued one chunk ahead, 11 the TMA-fed kernel (a producer
+     * warp streams 8-column chunks of the blocks and the matching stage
+     * values into shared memory, the other warps compute from there); -1
+     * before the first product.  The
+     * environment variable IRK_MATVEC_VARIANT=<0..11>, read when
      * a context makes its first product, pins the variant.  Every variant
      * gives the same result bit for bit. */
     int matvec_variant;

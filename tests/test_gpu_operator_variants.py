@@ -4,7 +4,8 @@ The autotuner picks one of several launches of the same product: the
 register-streaming kernel with different chunk widths and CTA sizes, the
 bulk-copy pipelined kernel with 2 or 3 shared-memory stages, and the
 register-streaming kernel with the block size fixed at compile time, one or
-four rows per thread.  All of them
+four rows per thread, and the TMA-fed kernel (a producer warp streaming
+column chunks and stage values into shared memory).  All of them
 accumulate every output in the same order, so each one, pinned with
 IRK_MATVEC_VARIANT, must give a result bitwise equal to variant 0's, and that
 result must match the FP64 oracle (1e-13 relative, the operator bar).
@@ -22,7 +23,7 @@ from _parity import rel
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-N_VARIANTS = 11
+N_VARIANTS = 14
 
 
 def dev(a):
@@ -56,10 +57,12 @@ def test_operator_variants_bitwise_equal(monkeypatch, krylov, kind, s, m):
     assert rel(outs[0], y_ref) <= 1e-13
 
 
-@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8, 9, 10])
+@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8, 9, 10, 11, 12, 13])
 def test_solve_with_pipelined_product_is_bitwise_equal(monkeypatch, variant):
     """The residual form (y = rhs - B x) of the pipelined kernel, inside a
-    full preconditioned solve: same W and iteration count as variant 0."""
+    full preconditioned solve: same W and iteration count as variant 0.
+    The compile-time variants (7, 9, 10, 11) there also take the kernels that
+    skip the zero low words of binary32 preconditioned vectors."""
     from paper_1701_07181_gb300 import irk
     P = make("2d", 3, 40)
     res = []
