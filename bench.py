@@ -394,6 +394,53 @@ def dirk_comparison(P, dev, rp, ci, J, M, dt=0.1, reps=3):
     return out
 
 
+# FP64 FMA units: 2 per SM per clock on GB300 (1.26 TFLOP/s at the 2.07 GHz
+# maximum SM clock), the bound of the binary64 operator product
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+
+
+def fp64_matvec_roofline(P, r, total_ms, n):
+    """Binary64 operator product: algorithmic flops 2s(r+1)m^2T + 2sm^2T +
+    2s^2 n per product over its measured time, against the FP64-pipe peak."""
+    s, T, m = P.s, P.T, P.m
+    flops = 2 * s * (r + 1) * m * m * T + 2 * s * m * m * T + 2 * s * s * T * m
+    avg = total_ms / max(1, n)
+    ach = flops / (avg * 1e9) if avg > 0 else None
+    return {"bound": "alu", "pipe": "fp64", "avg_ms": avg, "units": n, "alg_flops": flops, "achieved": ach,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS if ach else None,
+            "peak_source": "FP64 FMA unit count and max SM clock (152 x 2 x 2 x 2.07 GHz)"}
+
+
+def c2_rooflines(dev, hbm_peak, peak_kind, solves=3):
+    """Per-kernel times and rooflines on the 48000-tetrahedra workload (r = 4,
+    m = 50, s = 3; FP32 factors, double-float Krylov, four-colour order: the
+    preconditioner runs as level sweeps), from CUDA events over `solves`
+    solves after a warm-up."""
+    import torch
+    from paper_1701_07181_gb300 import inputs, irk
+    P = inputs.config("c2", seed=0)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    rp, ci, J, M, R = t(P.row_ptr), t(P.col_idx), t(P.J), t(P.M), t(P.R)
+    acc = dict(iters=[], n_factor=solves)
+    with irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec="fp32", krylov="df64",
+                    ordering="multicolor", timing=2) as S:
+        S.solve(R, 0.37, rtol=RTOL)  # warm-up and autotuning
+        S.stats()
+        for k in range(solves):
+            _, it, rr, rc = S.solve(R, 0.1 * (k + 1), rtol=RTOL)
+            acc["iters"].append(it)
+        st = S.stats()
+    for k in ("matvec_ms", "precond_ms", "ortho_ms", "factor_assemble_ms", "factor_products_ms",
+              "factor_inverse_ms", "sweep_fwd_ms", "sweep_bwd_ms", "n_matvec", "n_precond", "n_ortho"):
+        acc[k] = st[k]
+    acc["factor_ms"] = st["factor_assemble_ms"] + st["factor_products_ms"] + st["factor_inverse_ms"]
+    roof, kern = kernel_rooflines(P, 4, acc, hbm_peak, peak_kind, two_colour=st["sweep_two_colour"] == 1)
+    del rp, ci, J, M, R
+    return {"workload": "3D periodic 20^3 Kuhn grid, T=48000 tetrahedra, r=4, p=2 (m=50), s=3, dt 0.1/0.2/0.3",
+            "iters_per_solve": acc["iters"], "dominant": roof, "kernels": kern,
+            "sweep_form": "two-colour" if st["sweep_two_colour"] == 1 else "level sweeps (four colours)"}
+
+
 def kernel_rooflines(P, r, acc, hbm_peak, peak_kind, two_colour=False):
     """Per-kernel measured time (CUDA events, irk_options.timing) over the
     timed solves, algorithmic bytes or flops per unit, and the roofline of
@@ -460,6 +507,63 @@ def kernel_rooflines(P, r, acc, hbm_peak, peak_kind, two_colour=False):
     return roofline, kernels
 
 
+def batched_uneven(n, dev):
+    """Config-3 shape: n independent 2D meshes of 500-5000 triangles, p 1..3
+    (m 12/24/40), s 2..3, dt 0.1, all submitted at once (a backlog served by
+    continuous batching), against the same requests one at a time in plain
+    binary64 and in the same mixed precision."""
+    import torch
+    from paper_1701_07181_gb300 import inputs, serve
+    ub = inputs.batched_uneven(n, seed=5)
+    for q in ub:
+        q["arrival"] = 0.0
+    probs = serve.prepare(ub, dev)
+    torch.cuda.synchronize()
+    recs_b, sb = serve.run_stream(ub, probs, budget_bytes=120 << 30, max_wall_s=300)
+    recs_m, sm = serve.run_fifo(ub, probs, factor_prec="fp32", krylov="df64", ordering="multicolor")
+    recs_f, sf = serve.run_fifo(ub, probs)
+    out = {"requests": sb.n, "meshes": "2D periodic, 500-5000 triangles, p 1..3 (m 12/24/40), s 2..3, dt 0.1",
+           "batched": {"solves_per_s": sb.solves_per_s, "wall_s": sb.wall_s, "groups": sb.extra["groups"],
+                       "all_converged": all(r.status == 0 for r in recs_b)},
+           "fifo_mixed": {"solves_per_s": sm.solves_per_s, "wall_s": sm.wall_s,
+                          "solver": "same precision and order as the batched arm, one request at a time",
+                          "all_converged": all(r.status == 0 for r in recs_m)},
+           "fifo_plain_fp64": {"solves_per_s": sf.solves_per_s, "wall_s": sf.wall_s,
+                               "all_converged": all(r.status == 0 for r in recs_f)}}
+    del probs
+    return out
+
+
+def serving(n, dev, fifo_requests=10, rate=200.0, loads=(0.5, 1.0, 2.0), curve_requests=60):
+    """Config-4 shape: a Poisson stream (mean 200/s) of 2D/3D requests of
+    1k-40k elements, p 1..3, s 2..3, dt log-uniform [1e-3, 1], each request's
+    data generated on the device at admission (inside its latency).  The
+    first n requests of the 2000-request stream; FIFO arms (plain binary64,
+    and the batched arm's mixed precision one request at a time) on its first
+    fifo_requests; a load curve: the first curve_requests at offered loads of
+    0.5, 1 and 2 times the batched arm's measured service rate."""
+    from paper_1701_07181_gb300 import inputs, serve
+    full = inputs.serving_stream(2000, rate=rate, seed=11, elements=(1000, 40000), degrees=(1, 2, 3),
+                                 stages=(2, 3))
+    stream = full[:n]
+    recs_b, sb = serve.run_stream(stream, None, budget_bytes=120 << 30, max_wall_s=600)
+    head = stream[:fifo_requests]
+    recs_m, sm = serve.run_fifo(head, None, factor_prec="fp32", krylov="df64", ordering="multicolor")
+    recs_f, sf = serve.run_fifo(head, None)
+    curve = serve.load_curve(stream[:curve_requests], loads, sb.solves_per_s, budget_bytes=120 << 30,
+                             max_wall_s=300)
+    return {"requests": sb.n, "of_stream": len(full), "arrival_rate_per_s": rate,
+            "stream": "2D/3D periodic meshes of 1k-40k elements, p 1..3 (m 12..100), s 2..3, dt log-uniform "
+                      "[1e-3, 1]; data generated on the device at admission",
+            "batched": {"solves_per_s": sb.solves_per_s, "p50_ms": sb.p50_ms, "p99_ms": sb.p99_ms,
+                        "groups": sb.extra["groups"], "all_converged": all(r.status == 0 for r in recs_b)},
+            "fifo_mixed": {"requests": sm.n, "solves_per_s": sm.solves_per_s, "p50_ms": sm.p50_ms,
+                           "p99_ms": sm.p99_ms, "all_converged": all(r.status == 0 for r in recs_m)},
+            "fifo_plain_fp64": {"requests": sf.n, "solves_per_s": sf.solves_per_s, "p50_ms": sf.p50_ms,
+                                "p99_ms": sf.p99_ms, "all_converged": all(r.status == 0 for r in recs_f)},
+            "load_curve": curve}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -471,12 +575,21 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-dirk", action="store_true")
     ap.add_argument("--no-variants", action="store_true")
-    ap.add_argument("--uneven-requests", type=int, default=128)
-    ap.add_argument("--serving-requests", type=int, default=60)
+    ap.add_argument("--uneven-requests", type=int, default=512)
+    ap.add_argument("--serving-requests", type=int, default=120)
+    ap.add_argument("--fifo-requests", type=int, default=10)
+    ap.add_argument("--serving-only", action="store_true",
+                    help="run only the serving measurement (with --serving-requests up to 2000) and print it")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(3, args.warmup)
+    if args.serving_only:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"serving": serving(args.serving_requests, torch.device("cuda", 0),
+                                             fifo_requests=args.fifo_requests)}))
+        return 0
 
     import torch
     from paper_1701_07181_gb300 import inputs, irk
@@ -597,6 +710,7 @@ def main():
     # element order, and in the benchmark's two-colour order (the speed-up
     # of precision alone)
     plain = {}
+    fp64_mv = None
     for order in ("natural", "multicolor"):
         Sp = irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec="fp64", krylov="fp64",
                         ordering=order)
@@ -612,6 +726,14 @@ def main():
         barrier()
         plain_ms = max_over_ranks(p0.elapsed_time(p1))
         plain[order] = (world * args.plain_steps * len(DTS) / (plain_ms / 1000.0), plain_acc["iters"])
+        if order == "multicolor":
+            # the binary64 operator product's FP64-pipe fraction: one more
+            # step with per-kernel events (after the timed one)
+            Sp.set_timing(2)
+            Sp.stats()
+            step(Sp)
+            st = Sp.stats()
+            fp64_mv = fp64_matvec_roofline(P, 3, st["matvec_ms"], st["n_matvec"])
         Sp.close()
     plain_value = plain["natural"][0]
 
@@ -637,7 +759,8 @@ def main():
                                "speedup_of_value": value / plain_value,
                                "two_colour_order": {"value": plain["multicolor"][0],
                                                     "iters_per_solve": plain["multicolor"][1],
-                                                    "speedup_of_value": value / plain["multicolor"][0]}},
+                                                    "speedup_of_value": value / plain["multicolor"][0]},
+                               "fp64_matvec": fp64_mv},
             "natural_order_mixed": {"value": nat_value, "unit": UNIT, "iters_per_solve": nat_acc["iters"]},
             "roofline": roofline, "kernels": kernels, "e2e": e2e,
             "gpu_launches": acc["launches"], "clocks": clk,
@@ -646,42 +769,11 @@ def main():
         line["dirk_comparison"] = dirk_comparison(P, dev, rp, ci, J, M)
     if not args.no_variants and world == 1:
         line["precision_variants"] = precision_variants(dev)
+        line["c2_kernels"] = c2_rooflines(dev, peak, peak_kind)
     if not args.no_serving and world == 1 and args.uneven_requests > 0:
-        # batched uneven: independent 2D meshes of 500-5000 triangles, p 1..3,
-        # s 2..3, all submitted at once (continuous batching of a backlog)
-        from paper_1701_07181_gb300 import serve
-        ub = inputs.batched_uneven(args.uneven_requests, seed=5)
-        for q in ub:
-            q["arrival"] = 0.0
-        probs = serve.prepare(ub, dev)
-        torch.cuda.synchronize()
-        recs_b, sb = serve.run_stream(ub, probs, budget_bytes=120 << 30)
-        recs_f, sf = serve.run_fifo(ub, probs)
-        line["batched_uneven"] = {
-            "requests": sb.n, "meshes": "2D periodic, 500-5000 triangles, p 1..3 (m 12/24/40), s 2..3, dt 0.1",
-            "batched": {"solves_per_s": sb.solves_per_s, "wall_s": sb.wall_s, "groups": sb.extra["groups"],
-                        "all_converged": all(r.status == 0 for r in recs_b)},
-            "fifo_plain_fp64": {"solves_per_s": sf.solves_per_s, "wall_s": sf.wall_s,
-                                "all_converged": all(r.status == 0 for r in recs_f)},
-        }
-        del probs
+        line["batched_uneven"] = batched_uneven(args.uneven_requests, dev)
     if not args.no_serving and world == 1:
-        from paper_1701_07181_gb300 import serve
-        stream = inputs.serving_stream(args.serving_requests, rate=200.0, seed=11, elements=(1000, 10000),
-                                       degrees=(1, 2, 3), stages=(2, 3))
-        probs = serve.prepare(stream, dev)
-        torch.cuda.synchronize()
-        recs_b, sb = serve.run_stream(stream, probs, budget_bytes=120 << 30)
-        recs_f, sf = serve.run_fifo(stream, probs)
-        line["serving"] = {
-            "requests": sb.n, "arrival_rate_per_s": 200.0,
-            "stream": "2D/3D periodic meshes of 1k-10k elements, p 1..3, s 2..3, dt log-uniform [1e-3, 1]",
-            "batched": {"solves_per_s": sb.solves_per_s, "p50_ms": sb.p50_ms, "p99_ms": sb.p99_ms,
-                        "groups": sb.extra["groups"], "all_converged": all(r.status == 0 for r in recs_b)},
-            "fifo_plain_fp64": {"solves_per_s": sf.solves_per_s, "p50_ms": sf.p50_ms, "p99_ms": sf.p99_ms,
-                                "all_converged": all(r.status == 0 for r in recs_f)},
-        }
-        del probs
+        line["serving"] = serving(args.serving_requests, dev, fifo_requests=args.fifo_requests)
     if not args.no_cpu_baseline and world == 1:
         # the oracle as it stands, complete solves of the full workload, timed:
         # serial (one core) at dt = 0.01 (its cheapest solve: a bounded

@@ -12,6 +12,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <new>
 #include <utility>
 #include <vector>
@@ -603,16 +604,76 @@ int sync_group(irk_group *g) {
     return IRK_OK;
 }
 
+// Launch shapes of the group operator product: (columns of loads in flight
+// per thread, threads per CTA).  Every shape accumulates in the same order
+// (columns ascending, the same fold points), so all give the same bits; the
+// fastest per (m, s, arithmetic) is picked by timing them on a group's first
+// product (the product only writes its output, so repeating it is harmless)
+// and kept for the process.
+struct GMvShape {
+    int ch, threads;
+};
+const GMvShape kGMvShapes[] = {{8, 256}, {4, 256}, {2, 256}, {8, 128}, {4, 128}};
+const int kNumGMvShapes = 5;
+std::mutex g_gmv_mu;
+std::map<long long, int> g_gmv_choice;
+
 template <class AR, int S>
-void launch_g_matvec_s(irk_group *g, GMatvec &P) {
-    int groups = 256 / g->m;
-    int threads = (groups * g->m + 31) / 32 * 32;
+void run_g_matvec_shape(irk_group *g, const GMatvec &P, int v) {
+    const GMvShape sh = kGMvShapes[v];
+    const int groups = std::max(1, sh.threads / g->m);
+    const int threads = (groups * g->m + 31) / 32 * 32;
     long long grid = (g->n_elems + groups - 1) / groups;
     if (grid < 1) grid = 1;
-    if (S <= 3)
+    if (sh.ch == 8)
         k_g_matvec<AR, S, 8><<<(int)grid, threads, 0, g->stream>>>(P);
-    else
+    else if (sh.ch == 4)
         k_g_matvec<AR, S, 4><<<(int)grid, threads, 0, g->stream>>>(P);
+    else
+        k_g_matvec<AR, S, 2><<<(int)grid, threads, 0, g->stream>>>(P);
+}
+
+template <class AR, int S>
+void launch_g_matvec_s(irk_group *g, GMatvec &P) {
+    const long long key = ((long long)g->m << 20) | ((long long)S << 4) | g->df;
+    int v = -1;
+    {
+        std::lock_guard<std::mutex> lk(g_gmv_mu);
+        auto it = g_gmv_choice.find(key);
+        if (it != g_gmv_choice.end()) v = it->second;
+    }
+    if (v < 0 && g->n_elems >= 256) {
+        cudaEvent_t e0, e1;
+        cudaEventCreate(&e0);
+        cudaEventCreate(&e1);
+        float best = 1e30f;
+        for (int q = 0; q < kNumGMvShapes; ++q) {
+            if (kGMvShapes[q].threads < g->m) continue;
+            float t[3] = {1e30f, 1e30f, 1e30f};
+            bool launched = true;
+            for (int rep = 0; rep < 4 && launched; ++rep) {
+                cudaEventRecord(e0, g->stream);
+                run_g_matvec_shape<AR, S>(g, P, q);
+                launched = cudaGetLastError() == cudaSuccess;  // a shape that cannot launch is skipped
+                cudaEventRecord(e1, g->stream);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0 && launched) t[rep - 1] = ms;
+            }
+            std::sort(t, t + 3);
+            if (t[1] < best) {
+                best = t[1];
+                v = q;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lk(g_gmv_mu);
+        g_gmv_choice[key] = v;
+    }
+    if (v < 0) v = S <= 3 ? 0 : 1;  // small groups before a choice: the former default
+    run_g_matvec_shape<AR, S>(g, P, v);
 }
 
 template <class AR>

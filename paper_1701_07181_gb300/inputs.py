@@ -203,14 +203,81 @@ def block_size(dim: int, p: int) -> int:
     return (p + 1) * (p + 2) * (p + 3) // 6 * 5
 
 
+def _pattern_from_array(nb):
+    """bsr_pattern of a (T, r) neighbour array, vectorised: each row's
+    neighbours and the element itself, sorted."""
+    T, r = nb.shape
+    rows = np.sort(np.concatenate([nb, np.arange(T)[:, None]], axis=1), axis=1)
+    if np.any(rows[:, 1:] == rows[:, :-1]):
+        raise ValueError("an element has a repeated or self neighbour")
+    row_ptr = (np.arange(T + 1) * (r + 1)).astype(np.int32)
+    return row_ptr, rows.reshape(-1).astype(np.int32)
+
+
+def pattern_2d_periodic(nx: int, ny: int):
+    """bsr_pattern(mesh_2d_periodic(nx, ny)) without Python loops."""
+    if nx < 3 or ny < 3:
+        raise ValueError("nx, ny >= 3 so that no neighbour repeats")
+    y, x = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    y, x = y.reshape(-1), x.reshape(-1)
+    q = y * nx + x
+    nb = np.empty((2 * nx * ny, 3), np.int64)
+    nb[0::2] = np.stack([2 * (((y - 1) % ny) * nx + x) + 1, 2 * (y * nx + (x + 1) % nx) + 1, 2 * q + 1], axis=1)
+    nb[1::2] = np.stack([2 * (((y + 1) % ny) * nx + x), 2 * (y * nx + (x - 1) % nx), 2 * q], axis=1)
+    return _pattern_from_array(nb)
+
+
+def pattern_3d_periodic(nx: int, ny: int | None = None, nz: int | None = None):
+    """bsr_pattern(mesh_3d_periodic(nx, ny, nz)) without Python loops (the
+    same face rules as mesh_3d_periodic)."""
+    ny = nx if ny is None else ny
+    nz = nx if nz is None else nz
+    if min(nx, ny, nz) < 3:
+        raise ValueError("grid sizes >= 3 so that no neighbour repeats")
+    dims = np.array([nx, ny, nz])
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    c = np.stack([x.reshape(-1), y.reshape(-1), z.reshape(-1)], axis=1)  # cube-major order (z, y, x)
+
+    def cube_id(cc):
+        return (cc[:, 2] * ny + cc[:, 1]) * nx + cc[:, 0]
+
+    here = 6 * cube_id(c)
+    nb = np.empty((c.shape[0], 6, 4), np.int64)
+    for k, p in enumerate(_PERMS):
+        cp = c.copy()
+        cp[:, p[0]] = (cp[:, p[0]] + 1) % dims[p[0]]
+        cm = c.copy()
+        cm[:, p[2]] = (cm[:, p[2]] - 1) % dims[p[2]]
+        nb[:, k, 0] = here + _PERM_ID[(p[1], p[0], p[2])]
+        nb[:, k, 1] = here + _PERM_ID[(p[0], p[2], p[1])]
+        nb[:, k, 2] = 6 * cube_id(cp) + _PERM_ID[(p[1], p[2], p[0])]
+        nb[:, k, 3] = 6 * cube_id(cm) + _PERM_ID[(p[2], p[0], p[1])]
+    return _pattern_from_array(nb.reshape(-1, 4))
+
+
+def pattern_for_elements(T_target: int, dim: int):
+    """bsr_pattern(mesh_for_elements(T_target, dim)), vectorised."""
+    if dim == 2:
+        nx = max(3, round(math.sqrt(T_target / 2)))
+        ny = max(3, math.ceil(T_target / (2 * nx)))
+        return pattern_2d_periodic(nx, ny)
+    n = max(3, round((T_target / 6) ** (1.0 / 3.0)))
+    nz = max(3, math.ceil(T_target / (6 * n * n)))
+    return pattern_3d_periodic(n, n, nz)
+
+
 def make_problem_device(nbrs, m, s, dt, sigma, seed, device, name="device", meta=None):
     """The same block recipe drawn on the GPU (torch's seeded device
     generator, so the numbers differ from make_problem's numpy stream): for
     streams of many or large requests whose host generation would dominate.
-    J, M, R are CUDA float64 tensors; the pattern stays in numpy."""
+    J, M, R are CUDA float64 tensors; the pattern stays in numpy.  nbrs is a
+    neighbour list or an already built (row_ptr, col_idx) pattern."""
     import torch
-    row_ptr, col_idx = bsr_pattern(nbrs)
-    T = len(nbrs)
+    if isinstance(nbrs, tuple) and len(nbrs) == 2 and isinstance(nbrs[0], np.ndarray):
+        row_ptr, col_idx = nbrs
+    else:
+        row_ptr, col_idx = bsr_pattern(nbrs)
+    T = int(row_ptr.size - 1)
     nnzb = int(row_ptr[-1])
     gen = torch.Generator(device=device)
     gen.manual_seed(int(seed))

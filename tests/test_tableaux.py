@@ -15,3 +15,4 @@ def test_library_tableaux_equal_oracle(name):
     np.testing.assert_array_equal(b, bo)
     np.testing.assert_array_equal(c, co)
     assert np.all(np.triu(A, 1) == 0.0)
+
