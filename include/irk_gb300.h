@@ -419,10 +419,10 @@ typedef struct {
      * with eight columns of loads in flight per thread, 10 as 7 with the
      * block loads issued one chunk ahead, 11 the TMA-fed kernel (a producer
      * warp streams 8-column chunks of the blocks and the matching stage
-     * values into shared memory, the other warps compute from there); -1
-     * before the first product.  The
-     * environment variable IRK_MATVEC_VARIANT=<0..11>, read when
-     * a context makes its first product, pins the variant.  Every variant
+     * values into shared memory, the other warps compute from there), 12
+     * and 13 the TMA-fed kernel with 16-column chunks and two units in
+     * flight, and with 8-column chunks and three; -1 before the first
+     * product.  irk_kernel_options.matvec_variant pins the variant.  Every variant
      * gives the same result bit for bit. */
     int matvec_variant;
     /* with irk_options.timing = 1: device time of the kernels of the last
@@ -435,17 +435,60 @@ typedef struct {
     /* levels of the last factorisation whose block products ran as whole
      * staged rows (binary32 factors, every update of a lower block landing on
      * its row's diagonal block: Alg. 2 with the row's products independent);
-     * the environment variable IRK_NO_FUSED_FACTOR turns that kernel off */
+     * irk_kernel_options.factor_fused = 0 turns that kernel off */
     int factor_fused_levels;
     /* 1 when the last preconditioner application ran in the two-colour form:
      * two launches, the forward sweep of the second colour fused with its
      * diagonal-block products, then the backward sweep of the first colour
      * (two lower levels, the second without upper entries, as the
-     * two-colour order gives on a two-colourable mesh); 0 otherwise.  The
-     * environment variable IRK_NO_TWO_COLOUR turns that form off. */
+     * two-colour order gives on a two-colourable mesh); 0 otherwise.
+     * irk_kernel_options.sweep_two_colour = 0 turns that form off. */
     int sweep_two_colour;
 } irk_stats;
 IRK_API int irk_get_stats(const irk_ctx *ctx, irk_stats *out);
+
+/* Kernel choices of a context.  The defaults are the library's own choices;
+ * the other values select alternative launch forms of the same computation,
+ * for measurement and for the tests that compare the forms.  Every choice
+ * gives the same result bit for bit except where noted. */
+typedef struct {
+    int matvec_variant;     /* -1 (default): operator-product launch variant
+                               autotuned per (m, s, arithmetic); 0..13 pin one
+                               (see irk_stats.matvec_variant) */
+    int sweep_two_colour;   /* 1 (default): the two-launch preconditioner
+                               application where the element order allows it
+                               (see irk_stats.sweep_two_colour); 0: the level
+                               sweeps */
+    int sweep_shared_upper; /* 1 (default): backward sweeps read each upper
+                               block once for all stages where no factor update
+                               reaches the upper blocks; 0: once per stage */
+    int factor_fused;       /* 2 (default): staged-row block products, the
+                               compile-time form for block sizes 12/20/24/40/50;
+                               1: the generic staged-row kernel; 0: one lower
+                               entry at a time (the factors of the staged-row
+                               forms differ from it by binary32 rounding: they
+                               sum a row's Schur updates in one accumulator) */
+    int factor_gj_rows;     /* 1 (default): Gauss-Jordan inverses with one block
+                               row per thread in registers for block sizes
+                               12/20/24/40/50; 0: the shared-memory kernel */
+    int factor_gj_threads;  /* threads per CTA of the shared-memory inversion
+                               kernel, 32..256; 0 (default) = 128 */
+    int factor_gj_split_min;/* rows in a level from which its inversions run in
+                               their own launch after its products; 0
+                               (default) = 2048, 1 = always */
+    int arnoldi_form;       /* 0 (default): one launch per Arnoldi step, the
+                               vector kept in shared memory when a slice fits;
+                               1: the streaming form, 1024-thread CTAs; 2: the
+                               streaming form, 256-thread CTAs */
+} irk_kernel_options;
+
+/* Fill *ko with the defaults listed above. */
+IRK_API void irk_default_kernel_options(irk_kernel_options *ko);
+
+/* Set the kernel choices of a live context for the calls that follow (a
+ * pinned operator-product variant takes effect at the next product).
+ * IRK_ERR_INVALID for a NULL argument or a value out of range. */
+IRK_API int irk_set_kernel_options(irk_ctx *ctx, const irk_kernel_options *ko);
 
 /* Change irk_options.spin_limit of a live context for the calls that follow
  * (0 = the default of 2^20 polls).  IRK_ERR_INVALID for a negative value or

@@ -428,6 +428,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
     c->fprec = c->opt.factor_prec;
     c->nJ = (c->opt.stage_jacobians && s > 1) ? s : 1;
     c->spin = c->opt.spin_limit > 0 ? c->opt.spin_limit : IRK_DEFAULT_SPIN_LIMIT;
+    irk_default_kernel_options(&c->ko);
     cudaGetDevice(&c->dev);
     // pattern: host copy and validation
     c->h_rp.resize(T + 1);
@@ -861,6 +862,31 @@ int irk_step_outputs(irk_ctx *c, const double *W, const double *b, const double 
     const int rs = cuda_status(cudaStreamSynchronize(c->stream));
     cudaFree(tmp);
     return rc != IRK_OK ? rc : rs;
+}
+
+void irk_default_kernel_options(irk_kernel_options *ko) {
+    if (!ko) return;
+    ko->matvec_variant = -1;
+    ko->sweep_two_colour = 1;
+    ko->sweep_shared_upper = 1;
+    ko->factor_fused = 2;
+    ko->factor_gj_rows = 1;
+    ko->factor_gj_threads = 0;
+    ko->factor_gj_split_min = 0;
+    ko->arnoldi_form = 0;
+}
+
+int irk_set_kernel_options(irk_ctx *c, const irk_kernel_options *ko) {
+    if (!c || !ko) return IRK_ERR_INVALID;
+    if (ko->matvec_variant < -1 || ko->matvec_variant >= irk_matvec_variants() || ko->sweep_two_colour < 0 ||
+        ko->sweep_two_colour > 1 || ko->sweep_shared_upper < 0 || ko->sweep_shared_upper > 1 ||
+        ko->factor_fused < 0 || ko->factor_fused > 2 || ko->factor_gj_rows < 0 || ko->factor_gj_rows > 1 ||
+        (ko->factor_gj_threads != 0 && (ko->factor_gj_threads < 32 || ko->factor_gj_threads > 256)) ||
+        ko->factor_gj_split_min < 0 || ko->arnoldi_form < 0 || ko->arnoldi_form > 2)
+        return IRK_ERR_INVALID;
+    c->ko = *ko;
+    c->mv_variant = -1;  // re-chosen (or pinned) at the next product
+    return IRK_OK;
 }
 
 int irk_set_spin_limit(irk_ctx *c, int spin_limit) {

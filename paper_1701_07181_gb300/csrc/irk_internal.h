@@ -118,6 +118,7 @@ struct irk_ctx {
     unsigned long long *d_amax = nullptr;  // |x| bits of the largest magnitude seen
     double jmax = 0.0, mmax = 0.0;         // largest magnitudes of J and M
     int spin = IRK_DEFAULT_SPIN_LIMIT;     // effective irk_options.spin_limit
+    irk_kernel_options ko;                 // kernel choices (irk_set_kernel_options)
     int red_blocks = 0;
     irk_stats stats;
     long long launches = 0;
@@ -135,6 +136,8 @@ struct irk_ctx {
 };
 
 // ---- launchers (k_matvec.cu) ----
+// number of operator-product launch variants (irk_kernel_options.matvec_variant)
+int irk_matvec_variants();
 // y = B x (mode 0) or y = rhs - B x (mode 1); form: IRK_TRANSFORMED / UNTRANSFORMED;
 // x_f32: every value of x is binary32 (a preconditioned vector from binary32
 // factors), which lets the double-float kernel skip the low-word products

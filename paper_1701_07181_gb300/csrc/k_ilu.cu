@@ -57,17 +57,12 @@ int allow_max_smem(const void *func) {
 }
 
 // Threads per inversion CTA (k_factor_diag) and the level width from which a
-// level's inversions leave the product kernel; IRK_GJ_THREADS and
-// IRK_GJ_SPLIT_MIN override them (measurement).
-int env_int(const char *name, int dflt) {
-    const char *v = getenv(name);
-    return v ? atoi(v) : dflt;
+// level's inversions leave the product kernel (irk_kernel_options; 0 = the
+// defaults 128 and 2048).
+int gj_threads(const irk_ctx *c) {
+    return c->ko.factor_gj_threads > 0 ? std::max(32, std::min(256, c->ko.factor_gj_threads)) : 128;
 }
-int gj_threads() {
-    static const int t = std::max(32, std::min(256, env_int("IRK_GJ_THREADS", 128)));
-    return t;
-}
-int gj_split_min() { return env_int("IRK_GJ_SPLIT_MIN", 2048); }
+int gj_split_min(const irk_ctx *c) { return c->ko.factor_gj_split_min > 0 ? c->ko.factor_gj_split_min : 2048; }
 
 // ---------------------------------------------------------------------------
 // factor-storage loads (binary64, binary32 or bfloat16 storage)
@@ -2123,11 +2118,11 @@ void pc_free(PcSystem &P) {
 }
 
 // The register-row inversion for the block sizes it is compiled for
-// (IRK_GJ_ROWS=0 selects the shared-memory kernel); false otherwise.
+// (on = irk_kernel_options.factor_gj_rows; 0 selects the shared-memory
+// kernel); false otherwise.
 template <class C>
 static bool launch_diag_rows(cudaStream_t st, int n, int b, const int *rows, const int *diag, const C *vals, C *dinv,
-                             int *err) {
-    static const bool on = env_int("IRK_GJ_ROWS", 1) != 0;
+                             int *err, bool on) {
     if (!on) return false;
     switch (b) {
         case 12: k_factor_diag_rows<C, 12><<<n, 32, 0, st>>>(rows, diag, vals, dinv, err); return true;
@@ -2142,14 +2137,14 @@ static bool launch_diag_rows(cudaStream_t st, int n, int b, const int *rows, con
 // Warps per CTA of k_factor_fused for this pattern (8 or 16), or 0 when it
 // does not apply: updates not diagonal-only, odd block size (bulk copies want
 // 16-byte multiples), more phase-1 tiles than the warps' registers hold, or
-// the row's blocks do not fit in shared memory.  IRK_NO_FUSED_FACTOR turns it
-// off.
+// the row's blocks do not fit in shared memory; irk_kernel_options
+// factor_fused = 0 turns it off.
 static size_t fused_smem(const PcSystem &P) {
     const size_t stride = ((size_t)P.b * P.b * 4 + 127) / 128 * 128;
     return stride * (1 + 3 * (size_t)P.fused_r) + 128;
 }
-static int fused_warps(const PcSystem &P) {
-    if (P.fused_r <= 0 || (P.b & 1) || getenv("IRK_NO_FUSED_FACTOR") != nullptr) return 0;
+static int fused_warps(const PcSystem &P, int mode) {
+    if (P.fused_r <= 0 || (P.b & 1) || mode == 0) return 0;
     if (fused_smem(P) > 227 * 1024) return 0;
     const int items = P.fused_r * ((P.b + 15) / 16) * ((P.b + 7) / 8);
     if (items <= 8 * IRK_FUSED_TPW) return 8;
@@ -2171,8 +2166,8 @@ static bool launch_fused_b(int n, size_t smem, cudaStream_t st, const int *rows,
 }
 
 static void launch_fused(int nw, int n, size_t smem, cudaStream_t st, const int *rows, const PcSystem &P,
-                         float *vals, const float *dinv, int *err) {
-    if (getenv("IRK_FUSED_GENERIC") == nullptr &&
+                         float *vals, const float *dinv, int *err, int mode) {
+    if (mode == 2 &&
         (launch_fused_b<40>(n, smem, st, rows, P, vals, dinv, err) ||
          launch_fused_b<50>(n, smem, st, rows, P, vals, dinv, err) ||
          launch_fused_b<24>(n, smem, st, rows, P, vals, dinv, err) ||
@@ -2234,13 +2229,13 @@ static int factor_impl(irk_ctx *c, double dt) {
     const int nlev = (int)P.lo_ptr.size() - 1;
     c->stats.factor_fused_levels = 0;
     // staged whole-row products (binary32 factors, diagonal-only updates)
-    const int fused_nw = std::is_same<C, float>::value ? fused_warps(P) : 0;
+    const int fused_nw = std::is_same<C, float>::value ? fused_warps(P, c->ko.factor_fused) : 0;
     const size_t smem_f = fused_smem(P);
     // inversions in their own small CTAs: every row of level 0 (no lower
     // entries: nothing to update), and the rows of levels with at least
     // split_min rows after their products (one more launch per level)
-    const int gjt = std::max(gj_threads(), (b + 31) / 32 * 32);
-    const int split_min = gj_split_min();
+    const int gjt = std::max(gj_threads(c), (b + 31) / 32 * 32);
+    const int split_min = gj_split_min(c);
     const size_t smem_d = ((size_t)2 * b * b + (size_t)2 * b) * sizeof(C);
     for (int l = 0; l < nlev; ++l) {
         int n = P.lo_ptr[l + 1] - P.lo_ptr[l];
@@ -2252,7 +2247,7 @@ static int factor_impl(irk_ctx *c, double dt) {
                 tm = tmark_begin(c);
                 if (split && fused_nw > 0) {
                     launch_fused(fused_nw, n, smem_f, c->stream, lrows, P, (float *)P.d_vals, (const float *)P.d_dinv,
-                                 c->d_err);
+                                 c->d_err, c->ko.factor_fused);
                     c->stats.factor_fused_levels++;
                 } else
                     k_factor_level2<C><<<n, 256, smem4, c->stream>>>(lrows, b, P.d_rp, P.d_ci, P.d_diag,
@@ -2263,7 +2258,7 @@ static int factor_impl(irk_ctx *c, double dt) {
             if (split) {
                 tm = tmark_begin(c);
                 if (!launch_diag_rows<C>(c->stream, n, b, lrows, P.d_diag, (const C *)P.d_vals, (C *)P.d_dinv,
-                                         c->d_err))
+                                         c->d_err, c->ko.factor_gj_rows != 0))
                     k_factor_diag<C><<<n, gjt, smem_d, c->stream>>>(lrows, b, P.d_diag, (const C *)P.d_vals,
                                                                     (C *)P.d_dinv, c->d_err);
                 tmark_end(c, tm, 5);
@@ -2354,7 +2349,7 @@ static bool apply_two_colour(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, 
     tmark_end(c, tm, 6);
     tm = tmark_begin(c);
     const int s = c->s;
-    if (P.shared_upper && s >= 2 && s <= 4 && getenv("IRK_NO_SHARED_UPPER") == nullptr) {
+    if (P.shared_upper && s >= 2 && s <= 4 && c->ko.sweep_shared_upper) {
         const int n2 = P.up0_ptr[2] - P.up0_ptr[1];
         auto kern = s == 2 ? k_sweep_bu<AR, C, F, 2, B>
                            : (s == 3 ? k_sweep_bu<AR, C, F, 3, B> : k_sweep_bu<AR, C, F, 4, B>);
@@ -2383,7 +2378,7 @@ static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F
     c->stats.sweep_two_colour = 0;
     if (P.persistent) return apply_persistent<AR, C, F>(c, v, z, vals, dinv);
     if constexpr (std::is_same<C, float>::value && std::is_same<AR, ArDF>::value) {
-        if (P.two_colour && getenv("IRK_NO_TWO_COLOUR") == nullptr &&
+        if (P.two_colour && c->ko.sweep_two_colour &&
             (apply_two_colour<AR, C, F, 40>(c, v, z, vals, dinv) ||
              apply_two_colour<AR, C, F, 50>(c, v, z, vals, dinv) ||
              apply_two_colour<AR, C, F, 24>(c, v, z, vals, dinv) ||
@@ -2407,7 +2402,7 @@ static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F
     tm = tmark_begin(c);
     const size_t smem = (size_t)groups * b * sizeof(C);
     const int s = c->s;
-    if (P.shared_upper && s >= 2 && s <= 4 && getenv("IRK_NO_SHARED_UPPER") == nullptr) {
+    if (P.shared_upper && s >= 2 && s <= 4 && c->ko.sweep_shared_upper) {
         auto kern = s == 2 ? k_sweep_bwd_shared<AR, C, F, 2>
                            : (s == 3 ? k_sweep_bwd_shared<AR, C, F, 3> : k_sweep_bwd_shared<AR, C, F, 4>);
         const int nup0 = (int)P.up0_ptr.size() - 1;

@@ -479,22 +479,21 @@ __global__ void __launch_bounds__(1024) k_arnoldi_smem(long long N, long long ch
 // Launch shape of k_arnoldi: every CTA resident (cooperative launch).  Few
 // large CTAs keep the grid barrier (one atomic per CTA on one counter) and
 // the all-CTA reduction (every CTA reads every partial) short: one
-// 1024-thread CTA per SM by default; IRK_ARNOLDI_THREADS=256 selects
-// 256-thread CTAs, as many as fit.  At most IRK_PART_SLOTS / 2 CTAs (the
-// partial buffer holds two steps).  grid 0: no cooperative launch.
+// 1024-thread CTA per SM by default; irk_kernel_options.arnoldi_form = 2
+// selects 256-thread CTAs, as many as fit.  At most IRK_PART_SLOTS / 2 CTAs
+// (the partial buffer holds two steps).  grid 0: no cooperative launch.
 struct ArnoldiShape {
     int grid = -1, threads = 0;
 };
 
 template <class AR>
-static ArnoldiShape arnoldi_shape_for() {
+static ArnoldiShape arnoldi_shape_for(int threads) {
     ArnoldiShape sh;
     int dev = 0, coop = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    const char *env = getenv("IRK_ARNOLDI_THREADS");
-    sh.threads = (env && atoi(env) == 256) ? 256 : 1024;
+    sh.threads = threads;
     if (sh.threads == 256)
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_arnoldi<AR, 256>, 256, 0);
     else
@@ -505,10 +504,11 @@ static ArnoldiShape arnoldi_shape_for() {
 
 static ArnoldiShape arnoldi_shape(irk_ctx *c) {
     static std::mutex mu;
-    static ArnoldiShape cached[2];
+    static ArnoldiShape cached[2][2];  // [arithmetic][256-thread CTAs]
     std::lock_guard<std::mutex> lk(mu);
-    ArnoldiShape &sh = cached[c->df ? 1 : 0];
-    if (sh.grid < 0) sh = c->df ? arnoldi_shape_for<ArDF>() : arnoldi_shape_for<ArF64>();
+    const int small = c->ko.arnoldi_form == 2 ? 1 : 0;
+    ArnoldiShape &sh = cached[c->df ? 1 : 0][small];
+    if (sh.grid < 0) sh = c->df ? arnoldi_shape_for<ArDF>(small ? 256 : 1024) : arnoldi_shape_for<ArF64>(small ? 256 : 1024);
     return sh;
 }
 
@@ -518,7 +518,7 @@ static ArnoldiShape arnoldi_shape(irk_ctx *c) {
 // k_arnoldi_smem's launch, or false when its slices do not fit (or no
 // cooperative launch): one 1024-thread CTA per SM, chunk = ceil(N / SMs).
 static bool launch_arnoldi_smem(irk_ctx *c, int j, int restart, vec8 *w, int *rc) {
-    if (getenv("IRK_ARNOLDI_GLOBAL")) return false;
+    if (c->ko.arnoldi_form != 0) return false;
     static std::mutex mu;
     static int sms = -1, optin = 0, coop = 0;
     {

@@ -1117,11 +1117,8 @@ std::mutex g_tune_mu;
 std::map<long long, int> g_tune;
 
 int tune_key_variant(irk_ctx *c, const MatvecParams &P) {
-    // IRK_MATVEC_VARIANT=<0..13> pins the variant (tests compare them)
-    if (const char *pin = getenv("IRK_MATVEC_VARIANT")) {
-        const int v = atoi(pin);
-        if (v >= 0 && v < kNumMvVariants) return v;
-    }
+    // irk_kernel_options.matvec_variant pins the variant (tests compare them)
+    if (c->ko.matvec_variant >= 0 && c->ko.matvec_variant < kNumMvVariants) return c->ko.matvec_variant;
     const long long key = ((long long)c->m << 20) | ((long long)c->s << 4) | c->df;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
@@ -1198,6 +1195,8 @@ int launch_matvec_ps(irk_ctx *c, MatvecParams P) {
 }
 
 }  // namespace
+
+int irk_matvec_variants() { return kNumMvVariants; }
 
 // chosen variant of a context's class (-1 before the first product)
 int matvec_variant(const irk_ctx *c) { return c->mv_variant; }

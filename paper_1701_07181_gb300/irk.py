@@ -44,6 +44,13 @@ class Options(ctypes.Structure):
                 ("spin_limit", ctypes.c_int)]
 
 
+class KernelOptions(ctypes.Structure):
+    _fields_ = [("matvec_variant", ctypes.c_int), ("sweep_two_colour", ctypes.c_int),
+                ("sweep_shared_upper", ctypes.c_int), ("factor_fused", ctypes.c_int),
+                ("factor_gj_rows", ctypes.c_int), ("factor_gj_threads", ctypes.c_int),
+                ("factor_gj_split_min", ctypes.c_int), ("arnoldi_form", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int), ("levels_lower", ctypes.c_int),
                 ("levels_upper", ctypes.c_int), ("relres", ctypes.c_double),
@@ -62,7 +69,7 @@ EXPORTS = ["irk_default_options", "irk_setup", "irk_update_values", "irk_factor"
            "irk_strerror", "irk_apply_precond_noalloc", "irk_group_create", "irk_group_submit",
            "irk_group_step", "irk_group_query", "irk_group_collect", "irk_group_device_bytes",
            "irk_group_destroy", "irk_dirk_setup", "irk_dirk_step", "irk_dirk_destroy", "irk_set_timing",
-           "irk_step_outputs", "irk_set_spin_limit"]
+           "irk_step_outputs", "irk_set_spin_limit", "irk_default_kernel_options", "irk_set_kernel_options"]
 
 
 def load():
@@ -87,6 +94,9 @@ def load():
         lib.irk_get_stats.argtypes = [P, ctypes.POINTER(Stats)]
         lib.irk_set_timing.argtypes = [P, I]
         lib.irk_set_spin_limit.argtypes = [P, I]
+        lib.irk_default_kernel_options.argtypes = [ctypes.POINTER(KernelOptions)]
+        lib.irk_default_kernel_options.restype = None
+        lib.irk_set_kernel_options.argtypes = [P, ctypes.POINTER(KernelOptions)]
         lib.irk_step_outputs.argtypes = [P, P, P, P, D, P, P, I]
         lib.irk_destroy.argtypes = [P]
         lib.irk_destroy.restype = None
@@ -138,7 +148,8 @@ class Solver:
     def __init__(self, s, T, m, row_ptr, col_idx, J, M, A=None, precond="uncoupled",
                  factor_prec="fp64", krylov="fp64", formulation="transformed", restart=30,
                  max_iter=3000, shift=None, stream=None, timing=False, sweep="auto",
-                 ordering="natural", partitions=0, partition=None, stage_jacobians=False, spin_limit=0):
+                 ordering="natural", partitions=0, partition=None, stage_jacobians=False, spin_limit=0,
+                 kernel_options=None):
         lib = load()
         self._lib = lib
         self.s, self.T, self.m = int(s), int(T), int(m)
@@ -184,6 +195,8 @@ class Solver:
         if rc != IRK_OK:
             raise IrkError(rc, "irk_setup")
         self._h = h
+        if kernel_options:
+            self.set_kernel_options(**kernel_options)
 
     def _check(self, rc, what, allow_nc=False):
         if rc == IRK_OK or (allow_nc and rc == IRK_NOT_CONVERGED):
@@ -255,6 +268,17 @@ class Solver:
         bb = None if b is None else (ctypes.c_double * self.s)(*[float(x) for x in b])
         self._check(self._lib.irk_step_outputs(self._h, Wp, bb, u0p, float(dt), Kp, u1p, sp), "irk_step_outputs")
         return K, u1
+
+    def set_kernel_options(self, **kw):
+        """irk_set_kernel_options: the library's defaults with the given fields
+        (names of irk_kernel_options) changed."""
+        ko = KernelOptions()
+        self._lib.irk_default_kernel_options(ctypes.byref(ko))
+        for k, v in kw.items():
+            if k not in dict(KernelOptions._fields_):
+                raise KeyError(k)
+            setattr(ko, k, int(v))
+        self._check(self._lib.irk_set_kernel_options(self._h, ctypes.byref(ko)), "irk_set_kernel_options")
 
     def set_spin_limit(self, spin_limit):
         """irk_set_spin_limit: polls of a device wait on another thread block

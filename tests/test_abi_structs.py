@@ -1,5 +1,5 @@
-"""The ctypes structures of the binding mirror the C header's irk_options
-and irk_stats field for field (names, order and C types), so that a struct
+"""The ctypes structures of the binding mirror the C header's irk_options,
+irk_kernel_options and irk_stats field for field (names, order and C types), so that a struct
 passed across the ABI has the library's layout."""
 import ctypes
 import os
@@ -52,6 +52,14 @@ def test_options_mirror_header():
 def test_stats_mirror_header():
     hdr = header_fields("irk_stats")
     py = [(n, t) for n, t in irk.Stats._fields_]
+    assert [n for n, _ in hdr] == [n for n, _ in py]
+    for (n, ct), (_, pt) in zip(hdr, py):
+        assert same_type(CTYPE[ct], pt), (n, ct, pt)
+
+
+def test_kernel_options_mirror_header():
+    hdr = header_fields("irk_kernel_options")
+    py = [(n, t) for n, t in irk.KernelOptions._fields_]
     assert [n for n, _ in hdr] == [n for n, _ in py]
     for (n, ct), (_, pt) in zip(hdr, py):
         assert same_type(CTYPE[ct], pt), (n, ct, pt)

@@ -6,8 +6,8 @@ bulk-copy pipelined kernel with 2 or 3 shared-memory stages, and the
 register-streaming kernel with the block size fixed at compile time, one or
 four rows per thread, and the TMA-fed kernel (a producer warp streaming
 column chunks and stage values into shared memory).  All of them
-accumulate every output in the same order, so each one, pinned with
-IRK_MATVEC_VARIANT, must give a result bitwise equal to variant 0's, and that
+accumulate every output in the same order, so each one, pinned with the
+kernel option matvec_variant, must give a result bitwise equal to variant 0's, and that
 result must match the FP64 oracle (1e-13 relative, the operator bar).
 Cases: block sizes that are even (pipelined kernel applies) and odd (it falls
 back), s = 1..4, and a mesh large enough that every CTA of the pipelined
@@ -39,15 +39,14 @@ def make(kind, s, m, seed=3):
 @pytest.mark.parametrize("krylov", ["fp64", "df64"])
 @pytest.mark.parametrize("kind,s,m", [("2d", 3, 40), ("big2d", 3, 40), ("3d", 2, 20), ("chain", 1, 7),
                                       ("2d", 4, 12), ("chain", 2, 100), ("big2d", 2, 12)])
-def test_operator_variants_bitwise_equal(monkeypatch, krylov, kind, s, m):
+def test_operator_variants_bitwise_equal(krylov, kind, s, m):
     from paper_1701_07181_gb300 import irk
     P = make(kind, s, m)
     X = np.random.default_rng(7).standard_normal(P.s * P.T * P.m)
     outs = []
     for v in range(N_VARIANTS):
-        monkeypatch.setenv("IRK_MATVEC_VARIANT", str(v))
         with irk.Solver(P.s, P.T, P.m, dev(P.row_ptr), dev(P.col_idx), dev(P.J), dev(P.M), krylov=krylov,
-                        precond="none") as S:
+                        precond="none", kernel_options={"matvec_variant": v}) as S:
             y = S.apply_operator(dev(X), 0.37).cpu().numpy()
             assert S.stats()["matvec_variant"] == v
         outs.append(y)
@@ -58,7 +57,7 @@ def test_operator_variants_bitwise_equal(monkeypatch, krylov, kind, s, m):
 
 
 @pytest.mark.parametrize("variant", [4, 5, 6, 7, 8, 9, 10, 11, 12, 13])
-def test_solve_with_pipelined_product_is_bitwise_equal(monkeypatch, variant):
+def test_solve_with_pipelined_product_is_bitwise_equal(variant):
     """The residual form (y = rhs - B x) of the pipelined kernel, inside a
     full preconditioned solve: same W and iteration count as variant 0.
     The compile-time variants (7, 9, 10, 11) there also take the kernels that
@@ -67,8 +66,8 @@ def test_solve_with_pipelined_product_is_bitwise_equal(monkeypatch, variant):
     P = make("2d", 3, 40)
     res = []
     for v in (0, variant):
-        monkeypatch.setenv("IRK_MATVEC_VARIANT", str(v))
-        with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec="fp32", krylov="df64") as S:
+        with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec="fp32", krylov="df64",
+                        kernel_options={"matvec_variant": v}) as S:
             res.append(S.solve(P.R, P.dt, rtol=1e-8))
     np.testing.assert_array_equal(res[0][0], res[1][0])
     assert res[0][1] == res[1][1]

@@ -4,7 +4,7 @@
   element has two mutually adjacent neighbours), each stage's upper blocks
   are -dt J_ij and the backward sweep reads one copy for all stages; the
   application is bitwise equal to the per-stage sweep
-  (IRK_NO_SHARED_UPPER=1 forces the latter).
+  (irk_kernel_options.sweep_shared_upper = 0 forces the latter).
 * On a pattern with mutually adjacent elements the factor does modify upper
   blocks; the library keeps the per-stage sweep there, and the FP64
   application still matches the oracle.
@@ -27,17 +27,16 @@ def _irk():
 
 @pytest.mark.parametrize("fprec,krylov", [("fp32", "df64"), ("fp64", "fp64"), ("bf16", "df64")])
 @pytest.mark.parametrize("kind,s,m", [("2d", 3, 40), ("3d", 2, 20), ("2d", 4, 12)])
-def test_shared_upper_sweep_is_bitwise_equal(monkeypatch, fprec, krylov, kind, s, m):
+def test_shared_upper_sweep_is_bitwise_equal(fprec, krylov, kind, s, m):
     irk = _irk()
     nb = inputs.mesh_2d_periodic(9, 7) if kind == "2d" else inputs.mesh_3d_periodic(3, 3, 4)
     P = inputs.make_problem(nb, m, s, 0.3, 4.0, seed=2)
     V = np.random.default_rng(8).standard_normal(P.s * P.T * P.m)
     out = []
-    for off in ("", "1"):
-        if off:
-            monkeypatch.setenv("IRK_NO_SHARED_UPPER", "1")
+    for shared in (1, 0):
         with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec=fprec, krylov=krylov,
-                        sweep="levels", ordering="multicolor") as S:
+                        sweep="levels", ordering="multicolor",
+                        kernel_options={"sweep_shared_upper": shared}) as S:
             S.factor(0.3)
             out.append(S.apply_precond(V))
     np.testing.assert_array_equal(out[0], out[1])
@@ -61,29 +60,26 @@ def test_mutual_neighbours_fall_back_and_match_oracle():
 @pytest.mark.parametrize("fprec", ["fp32", "bf16"])
 @pytest.mark.parametrize("kind,s,m,shared", [("2d", 3, 40, True), ("3d", 2, 20, True), ("2d", 4, 12, True),
                                              ("3d", 3, 50, True), ("chain", 1, 24, True), ("2d", 3, 40, False)])
-def test_two_colour_application_is_bitwise_equal(monkeypatch, fprec, kind, s, m, shared):
+def test_two_colour_application_is_bitwise_equal(fprec, kind, s, m, shared):
     """In the two-colour order the first colour's rows have no lower entries
     (y = v there) and the second colour's no upper entries (z = D^{-1} y right
     after the forward row), so the application runs as two launches instead
     of four.  It keeps every dot product's arithmetic: the preconditioned
     vector and a whole FGMRES solve are bitwise equal to the level sweeps'
-    (IRK_NO_TWO_COLOUR=1), with two launches fewer per application.  Shared
-    upper blocks for all stages, and per-stage upper blocks (s = 1, and
-    IRK_NO_SHARED_UPPER=1).  The Kuhn-tetrahedra meshes need four colours
+    (kernel option sweep_two_colour = 0), with two launches fewer per
+    application.  Shared upper blocks for all stages, and per-stage upper
+    blocks (s = 1, and kernel option sweep_shared_upper = 0).  The Kuhn-tetrahedra meshes need four colours
     in first-fit order: there the level sweeps run either way."""
     irk = _irk()
     nb = {"2d": inputs.mesh_2d_periodic(9, 7), "3d": inputs.mesh_3d_periodic(3, 3, 4),
           "chain": inputs.mesh_1d_chain(38)}[kind]
-    if not shared:
-        monkeypatch.setenv("IRK_NO_SHARED_UPPER", "1")
     P = inputs.make_problem(nb, m, s, 0.3, 4.0, seed=2)
     V = np.random.default_rng(8).standard_normal(P.s * P.T * P.m)
     out, sol, launches = [], [], []
     for off in ("", "1"):
-        if off:
-            monkeypatch.setenv("IRK_NO_TWO_COLOUR", "1")
+        ko = {"sweep_shared_upper": 1 if shared else 0, "sweep_two_colour": 0 if off else 1}
         with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec=fprec, krylov="df64",
-                        sweep="levels", ordering="multicolor", timing=True) as S:
+                        sweep="levels", ordering="multicolor", timing=True, kernel_options=ko) as S:
             S.factor(0.3)
             out.append(S.apply_precond(V))
             W, it, rr, rc = S.solve(P.R, 0.3, rtol=1e-8)

@@ -17,21 +17,21 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-def test_deferred_timing_totals_match_per_solve_timing(monkeypatch):
+def test_deferred_timing_totals_match_per_solve_timing():
     from paper_1701_07181_gb300 import irk
-    monkeypatch.setenv("IRK_MATVEC_VARIANT", "0")  # no autotuning launches in either context
+    ko = {"matvec_variant": 0}  # no autotuning launches in either context
     P = inputs.make_problem(inputs.mesh_2d_periodic(12, 10), 20, 3, 0.2, 4.0, seed=4)
     dts = (0.05, 0.2)
     per, sols = [], []
     with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec="fp32", krylov="df64",
-                    ordering="multicolor", timing=1) as S:
+                    ordering="multicolor", timing=1, kernel_options=ko) as S:
         for dt in dts:
             W, it, rr, rc = S.solve(P.R, dt, rtol=1e-8)
             assert rc == 0
             per.append(S.stats())
             sols.append(W)
     with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec="fp32", krylov="df64",
-                    ordering="multicolor", timing=2) as S:
+                    ordering="multicolor", timing=2, kernel_options=ko) as S:
         S.stats()  # nothing pending yet
         out = [S.solve(P.R, dt, rtol=1e-8)[0] for dt in dts]
         tot = S.stats()
@@ -50,19 +50,19 @@ def test_deferred_timing_totals_match_per_solve_timing(monkeypatch):
     assert again["n_matvec"] == 0 and again["kernel_launches"] == 0
 
 
-def test_set_timing_samples_calls(monkeypatch):
+def test_set_timing_samples_calls():
     """irk_set_timing switches the events on and off between calls: marks
     recorded under timing = 2 survive a switch to 0 and are reported by the
     next irk_get_stats under timing = 2; calls made with timing 0 add none."""
     from paper_1701_07181_gb300 import irk
-    monkeypatch.setenv("IRK_MATVEC_VARIANT", "0")
+    ko = {"matvec_variant": 0}
     P = inputs.make_problem(inputs.mesh_2d_periodic(12, 10), 20, 3, 0.2, 4.0, seed=4)
     with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec="fp32", krylov="df64",
-                    ordering="multicolor", timing=1) as S:
+                    ordering="multicolor", timing=1, kernel_options=ko) as S:
         S.solve(P.R, 0.05, rtol=1e-8)
         one = S.stats()
     with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, factor_prec="fp32", krylov="df64",
-                    ordering="multicolor", timing=2) as S:
+                    ordering="multicolor", timing=2, kernel_options=ko) as S:
         S.stats()
         S.solve(P.R, 0.05, rtol=1e-8)   # timed
         S.set_timing(0)
