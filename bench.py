@@ -338,6 +338,42 @@ def precision_variants(dev):
     return out
 
 
+def ortho_compare(P, dev, rp, ci, J, M, R, steps=2):
+    """The benchmark configuration with modified Gram-Schmidt and with CGS2
+    orthogonalisation: solves/s over `steps` steps of the three dt, the
+    Arnoldi device time per solve (CUDA events on every kernel of those
+    steps) and the iteration counts."""
+    import torch
+    from paper_1701_07181_gb300 import irk
+    out = {}
+    for ortho in ("mgs", "cgs2"):
+        with irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec="fp32", krylov="df64",
+                        ordering="multicolor", orthogonalization=ortho) as S:
+            for dt in DTS:
+                S.solve(R, dt, rtol=RTOL)  # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            its = []
+            e0.record()
+            for _ in range(steps):
+                for dt in DTS:
+                    its.append(S.solve(R, dt, rtol=RTOL)[1])
+            e1.record()
+            torch.cuda.synchronize()
+            wall = e0.elapsed_time(e1)
+            S.set_timing(2)
+            S.stats()
+            for dt in DTS:
+                S.solve(R, dt, rtol=RTOL)
+            st = S.stats()
+        out[ortho] = {"solves_per_s": steps * len(DTS) / (wall / 1000.0), "iters_per_solve": its[: len(DTS)],
+                      "arnoldi_ms_per_solve": st["ortho_ms"] / len(DTS),
+                      "arnoldi_ms_per_iteration": st["ortho_ms"] / max(1, st["n_ortho"])}
+    out["note"] = ("benchmark configuration (FP32 factors, double-float Krylov, two-colour order); Arnoldi "
+                   "times from per-kernel CUDA events on one step of the three dt after the timed steps")
+    return out
+
+
 def dirk_comparison(P, dev, rp, ci, J, M, dt=0.1, reps=3):
     """Equal-order IRK vs DIRK steps of M u' = J u on the benchmark mesh
     (Sec. 5's comparison): RADAU23 vs DIRK33 and RADAU35 vs ESDIRK65.  One
@@ -767,6 +803,7 @@ def main():
             "last_solve": {"iters": st_last["iters"], "relres": st_last["relres"]}}
     if not args.no_dirk and world == 1:
         line["dirk_comparison"] = dirk_comparison(P, dev, rp, ci, J, M)
+        line["orthogonalization"] = ortho_compare(P, dev, rp, ci, J, M, R)
     if not args.no_variants and world == 1:
         line["precision_variants"] = precision_variants(dev)
         line["c2_kernels"] = c2_rooflines(dev, peak, peak_kind)

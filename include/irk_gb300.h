@@ -99,6 +99,14 @@ enum irk_krylov_arith { IRK_KRYLOV_FP64 = 0, IRK_KRYLOV_DF64 = 1 };
 
 enum irk_formulation { IRK_TRANSFORMED = 0, IRK_UNTRANSFORMED = 1 };
 
+/* Orthogonalisation of the Arnoldi process (Sec. 4 does not fix it).  MGS:
+ * modified Gram-Schmidt, j + 2 dependent inner products in step j.  CGS2:
+ * classical Gram-Schmidt applied twice: all inner products of a pass at
+ * once, two passes, so two grid-wide reductions per step whatever j; it
+ * reads the basis three times against MGS's twice.  Both keep the basis
+ * orthonormal to working precision; the iterates differ by rounding. */
+enum irk_orthogonalization { IRK_ORTHO_MGS = 0, IRK_ORTHO_CGS2 = 1 };
+
 /* Scheduling of the preconditioner's block triangular sweeps.  AUTO: one
  * persistent launch per application, rows synchronised through published
  * values (block size <= 128), unless the levels are wide (on average >= 4096
@@ -158,6 +166,8 @@ typedef struct {
                           leaves the kernel; the call returns IRK_ERR_TIMEOUT
                           and the context stays usable.  0 (default) = 2^20
                           polls (about a second); must be >= 0. */
+    int orthogonalization; /* enum irk_orthogonalization (default IRK_ORTHO_MGS);
+                          irk_group_create accepts MGS only */
 } irk_options;
 
 /* Fill *opt with the defaults listed above. */

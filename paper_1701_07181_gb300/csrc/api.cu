@@ -377,6 +377,7 @@ void irk_default_options(irk_options *o) {
     o->partition = nullptr;
     o->stage_jacobians = 0;
     o->spin_limit = 0;
+    o->orthogonalization = IRK_ORTHO_MGS;
 }
 
 const char *irk_strerror(int code) {
@@ -415,7 +416,8 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
         c->opt.factor_prec > IRK_FACTOR_BF16 || c->opt.krylov_arith < 0 || c->opt.krylov_arith > 1 ||
         c->opt.formulation < 0 || c->opt.formulation > 1 || c->opt.sweep < 0 || c->opt.sweep > 1 ||
         c->opt.ordering < 0 || c->opt.ordering > 1 || c->opt.partitions < 0 || c->opt.stage_jacobians < 0 ||
-        c->opt.stage_jacobians > 1 || c->opt.spin_limit < 0 ||
+        c->opt.stage_jacobians > 1 || c->opt.spin_limit < 0 || c->opt.orthogonalization < 0 ||
+        c->opt.orthogonalization > IRK_ORTHO_CGS2 ||
         (c->opt.precond == IRK_PC_UNCOUPLED && c->opt.formulation != IRK_TRANSFORMED)) {
         delete c;
         return IRK_ERR_INVALID;

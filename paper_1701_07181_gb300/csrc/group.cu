@@ -918,7 +918,7 @@ int irk_group_create(irk_group **out, int s, const double *A, int m, int max_ele
         (o.factor_prec != IRK_FACTOR_FP32 && o.factor_prec != IRK_FACTOR_FP64) || o.krylov_arith < 0 ||
         o.krylov_arith > 1 || o.restart < 1 || o.restart > IRK_MAX_RESTART || o.partitions > 1 ||
         (opt && opt->partition) || o.ordering < 0 || o.ordering > 1 || m > 128 || o.stage_jacobians != 0 ||
-        o.spin_limit < 0) {
+        o.spin_limit < 0 || o.orthogonalization != IRK_ORTHO_MGS) {
         delete g;
         return IRK_ERR_INVALID;
     }

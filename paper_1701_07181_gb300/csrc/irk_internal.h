@@ -173,7 +173,7 @@ int launch_convert_blocks(irk_ctx *c, const double *src, vec8 *dst, long long nb
 #define IRK_SCAL_SLOTS 128
 #define IRK_SCAL_BYTES 32
 // entries of the per-CTA partial-sum buffer d_part (>= red_blocks)
-#define IRK_PART_SLOTS 4096
+#define IRK_PART_SLOTS 16384
 #define IRK_MAX_RESTART 60
 // w <- w - h[hprev_slot] vprev (if vprev), then slot out = <w, v> (self: v = w;
 // take_sqrt: store the square root); H_out (if non-null) receives the value.

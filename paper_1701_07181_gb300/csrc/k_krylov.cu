@@ -476,6 +476,195 @@ __global__ void __launch_bounds__(1024) k_arnoldi_smem(long long N, long long ch
     }
 }
 
+// ---------------------------------------------------------------------------
+// The Arnoldi step by classical Gram-Schmidt applied twice (CGS2), in one
+// cooperative launch with two grid-wide reductions instead of j + 2:
+//   pass 1: h_i = <w, v_i>, i = 0..j                            (reduction 1)
+//   pass 2: w' = w - sum_i h_i v_i; q_i = <w', v_i>; ||w'||^2    (reduction 2)
+//   pass 3: v_{j+1} = (w' - sum_i q_i v_i) / h_{j+1,j},
+// with H[i][j] = h_i + q_i and h_{j+1,j}^2 = ||w'||^2 - sum_i q_i^2: w' minus
+// the final vector is V q, in the span of the orthonormal v_i, so the final
+// norm follows without a third reduction (q is of the order of pass 2's
+// rounding error: no cancellation).  Each CTA owns a contiguous slice of w,
+// kept in shared memory when it fits (SM), else updated in place in global
+// memory.  The basis is read three times (twice with MGS), in exchange for
+// the j dependent grid-wide reductions MGS needs.  Every accumulator adds its
+// elements in a fixed order, warps reduce with a fixed shuffle tree, and
+// every CTA sums the CTAs' partials in the same order: deterministic.
+// VM: the most basis vectors this instantiation handles (j + 1 <= VM); U:
+// elements a thread works on at once.
+template <class AR, int VM, int NT, int U, bool SM>
+__global__ void __launch_bounds__(NT) k_arnoldi_cgs2(long long N, long long chunk, int j, int R, vec8 *w,
+                                                     const vec8 *V, double *H, double *cs, double *sn, double *g,
+                                                     double *est, vec8 *part, unsigned *bar, int *err,
+                                                     double *status, int spin) {
+    typedef typename AR::val val;
+    typedef typename AR::acc acc;
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ val s_w[NW][VM + 1];  // per-warp sums
+    __shared__ double s_d[VM + 1];   // reduced values (binary64)
+    __shared__ val s_c[VM];          // the current pass's coefficients, negated
+    __shared__ int s_ok;
+    const int nv = j + 1;
+    const long long c0 = (long long)blockIdx.x * chunk;
+    const long long c1 = c0 + chunk < N ? c0 + chunk : N;
+    const int len = c1 > c0 ? (int)(c1 - c0) : 0;
+    vec8 *ws = SM ? reinterpret_cast<vec8 *>(smem_raw) : w + c0;
+    const vec8 *Vc = V + c0;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (SM) {
+        for (int e = threadIdx.x; e < len; e += NT) ws[e] = w[c0 + e];
+        __syncthreads();
+    }
+    acc a[VM];
+    acc an = AR::zero();
+    // the CTA's sums of a[0..cnt) (and of an as value cnt when with_norm) into
+    // part[base + i*grid + b]; after the grid barrier every CTA's totals in
+    // s_d[0..cnt + with_norm); false on a timeout
+    auto reduce = [&](int cnt, bool with_norm, long long base) -> bool {
+        const int tot_n = cnt + (with_norm ? 1 : 0);
+#pragma unroll
+        for (int i = 0; i < VM + 1; ++i) {
+            if (i >= tot_n) break;
+            val v = (i < VM && i < cnt) ? AR::value(a[i < VM ? i : 0]) : AR::value(an);
+            for (int d = 16; d > 0; d >>= 1) v = AR::add(v, AR::shfl_down(v, d));
+            if (lane == 0) s_w[wid][i] = v;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < tot_n; i += NT) {
+            acc t = AR::zero();
+            for (int q = 0; q < NW; ++q) AR::add_to(t, s_w[q][i]);
+            AR::st(part + base + (long long)i * gridDim.x + blockIdx.x, AR::value(t));
+        }
+        if (!grid_sync(bar, err, &s_ok, spin)) return false;
+        for (int i = wid; i < tot_n; i += NW) {
+            const val tot = warp_sum_partials<AR>(part + base + (long long)i * gridDim.x, (int)gridDim.x);
+            if (lane == 0) {
+                double d = AR::to_double(tot);
+                if (!isfinite(d)) {
+                    if (blockIdx.x == 0) atomicOr(err, IRK_DEV_ERR_NONFINITE);
+                    d = 0.0;
+                }
+                s_d[i] = d;
+            }
+        }
+        __syncthreads();
+        return true;
+    };
+    auto set_coefs = [&]() {
+        for (int i = threadIdx.x; i < nv; i += NT) {
+            const double d = s_d[i];
+            const float hh = (float)d;
+            s_c[i] = AR::neg(AR::coef(d, hh, (float)(d - (double)hh)));
+        }
+        __syncthreads();
+    };
+    // Each thread takes U elements at a time (e, e + NT, ...) and issues the
+    // loads of all of them and all basis vectors before using any, so U (j+1)
+    // loads are in flight per thread.
+    // pass 1: h_i = <w, v_i>
+#pragma unroll
+    for (int i = 0; i < VM; ++i) a[i] = AR::zero();
+    for (int e = threadIdx.x; e < len; e += U * NT) {
+        val wv[U], v[U][VM];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int ee = e + u * NT;
+            wv[u] = ee < len ? AR::ldv(ws + ee) : AR::from_float(0.f);
+#pragma unroll
+            for (int i = 0; i < VM; ++i)
+                v[u][i] = (i < nv && ee < len) ? AR::ld(Vc + (long long)i * N + ee) : AR::from_float(0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+            for (int i = 0; i < VM; ++i)
+                if (i < nv && e + u * NT < len) AR::fma(a[i], wv[u], v[u][i]);
+    }
+    if (!reduce(nv, false, 0)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) arnoldi_status(status, 0.0, 0.0, err);
+        return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        for (int i = 0; i < nv; ++i) H[i * R + j] = s_d[i];
+    set_coefs();
+    // pass 2: w' = w - V h; q_i = <w', v_i>; ||w'||^2 (the basis values
+    // loaded once serve both)
+#pragma unroll
+    for (int i = 0; i < VM; ++i) a[i] = AR::zero();
+    for (int e = threadIdx.x; e < len; e += U * NT) {
+        val wv[U], v[U][VM];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int ee = e + u * NT;
+            wv[u] = ee < len ? AR::ldv(ws + ee) : AR::from_float(0.f);
+#pragma unroll
+            for (int i = 0; i < VM; ++i)
+                v[u][i] = (i < nv && ee < len) ? AR::ld(Vc + (long long)i * N + ee) : AR::from_float(0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int ee = e + u * NT;
+            if (ee >= len) break;
+            acc t = AR::zero();
+            AR::add_to(t, wv[u]);
+#pragma unroll
+            for (int i = 0; i < VM; ++i)
+                if (i < nv) AR::fma(t, s_c[i], v[u][i]);
+            const val wn = AR::value(t);
+            AR::st(ws + ee, wn);
+#pragma unroll
+            for (int i = 0; i < VM; ++i)
+                if (i < nv) AR::fma(a[i], wn, v[u][i]);
+            AR::fma(an, wn, wn);
+        }
+    }
+    if (!reduce(nv, true, (long long)(VM + 1) * gridDim.x)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) arnoldi_status(status, 0.0, 0.0, err);
+        return;
+    }
+    double qq = 0.0;
+    for (int i = 0; i < nv; ++i) qq += s_d[i] * s_d[i];
+    const double n2 = s_d[nv] - qq;
+    const double hn = n2 > 0.0 ? sqrt(n2) : 0.0;
+    const double inv = hn != 0.0 ? 1.0 / hn : 0.0;
+    const float ih = (float)inv;
+    const val iv = AR::coef(inv, ih, (float)(inv - (double)ih));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int i = 0; i < nv; ++i) H[i * R + j] += s_d[i];
+        H[(j + 1) * R + j] = hn;
+    }
+    set_coefs();
+    // pass 3: v_{j+1} = (w' - V q) / h_{j+1,j}
+    for (int e = threadIdx.x; e < len; e += U * NT) {
+        val wv[U], v[U][VM];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int ee = e + u * NT;
+            wv[u] = ee < len ? AR::ldv(ws + ee) : AR::from_float(0.f);
+#pragma unroll
+            for (int i = 0; i < VM; ++i)
+                v[u][i] = (i < nv && ee < len) ? AR::ld(Vc + (long long)i * N + ee) : AR::from_float(0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int ee = e + u * NT;
+            if (ee >= len) break;
+            acc t = AR::zero();
+            AR::add_to(t, wv[u]);
+#pragma unroll
+            for (int i = 0; i < VM; ++i)
+                if (i < nv) AR::fma(t, s_c[i], v[u][i]);
+            AR::st(w + c0 + ee, AR::mul(AR::value(t), iv));
+        }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        givens_col(j, R, H, cs, sn, g, est, err);
+        arnoldi_status(status, *est, hn, err);
+    }
+}
+
 // Launch shape of k_arnoldi: every CTA resident (cooperative launch).  Few
 // large CTAs keep the grid barrier (one atomic per CTA on one counter) and
 // the all-CTA reduction (every CTA reads every partial) short: one
@@ -553,8 +742,59 @@ static bool launch_arnoldi_smem(irk_ctx *c, int j, int restart, vec8 *w, int *rc
     return true;
 }
 
+// One CGS2 launch (k_arnoldi_cgs2): one CTA per SM, the w slice in shared
+// memory when it fits; threads per CTA by the registers VM accumulators need.
+// false when no cooperative launch is possible.
+template <class AR, int VM, int NT, int U>
+static bool launch_cgs2_vm(irk_ctx *c, int j, int restart, vec8 *w, int *rc) {
+    static std::mutex mu;
+    static int sms = -1, optin = 0, coop = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (sms < 0) {
+            int dev = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+            cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+        }
+    }
+    if (!coop || sms <= 0 || (long long)sms * 2 * (VM + 1) > IRK_PART_SLOTS) return false;
+    long long N = c->N;
+    long long chunk = (N + sms - 1) / sms;
+    chunk = (chunk + 1) / 2 * 2;
+    const size_t static_smem = sizeof(typename AR::val) * ((NT / 32) * (VM + 1) + VM) + 8 * (VM + 1) + 64;
+    const bool fits = (size_t)chunk * sizeof(vec8) + static_smem + 1024 <= (size_t)optin;
+    const void *fn = fits ? (const void *)k_arnoldi_cgs2<AR, VM, NT, U, true>
+                          : (const void *)k_arnoldi_cgs2<AR, VM, NT, U, false>;
+    const size_t smem = fits ? (size_t)chunk * sizeof(vec8) : 0;
+    if (fits && irk_allow_max_smem(fn)) return false;
+    int jj = j, R = restart, spin = c->spin;
+    const vec8 *V = c->d_V;
+    double *est = &scal(c, 1)->d;
+    vec8 *part = reinterpret_cast<vec8 *>(c->d_part);
+    double *status = irk_status_ptr(c);
+    void *args[] = {&N, &chunk, &jj, &R, &w, &V, &c->d_H, &c->d_cs, &c->d_sn, &c->d_g, &est, &part, &c->d_gbar,
+                    &c->d_err, &status, &spin};
+    *rc = cuda_status(cudaLaunchCooperativeKernel(fn, sms, NT, args, smem, c->stream));
+    c->launches++;
+    return true;
+}
+
+template <class AR>
+static bool launch_cgs2(irk_ctx *c, int j, int restart, vec8 *w, int *rc) {
+    if (j + 1 <= 4) return launch_cgs2_vm<AR, 4, 1024, 4>(c, j, restart, w, rc);
+    if (j + 1 <= 8) return launch_cgs2_vm<AR, 8, 512, 4>(c, j, restart, w, rc);
+    if (j + 1 <= 16) return launch_cgs2_vm<AR, 16, 256, 2>(c, j, restart, w, rc);
+    if (j + 1 <= 32) return launch_cgs2_vm<AR, 32, 256, 1>(c, j, restart, w, rc);
+    return false;
+}
+
 int launch_arnoldi(irk_ctx *c, int j, int restart, vec8 *w) {
     int rc = IRK_OK;
+    if (c->opt.orthogonalization == IRK_ORTHO_CGS2 &&
+        (c->df ? launch_cgs2<ArDF>(c, j, restart, w, &rc) : launch_cgs2<ArF64>(c, j, restart, w, &rc)))
+        return rc;
     if (launch_arnoldi_smem(c, j, restart, w, &rc)) return rc;
     const ArnoldiShape sh = arnoldi_shape(c);
     if (sh.grid <= 0) return IRK_ERR_INVALID;

@@ -41,7 +41,7 @@ class Options(ctypes.Structure):
                 ("stream", ctypes.c_void_p), ("timing", ctypes.c_int), ("sweep", ctypes.c_int),
                 ("ordering", ctypes.c_int), ("partitions", ctypes.c_int),
                 ("partition", ctypes.POINTER(ctypes.c_int32)), ("stage_jacobians", ctypes.c_int),
-                ("spin_limit", ctypes.c_int)]
+                ("spin_limit", ctypes.c_int), ("orthogonalization", ctypes.c_int)]
 
 
 class KernelOptions(ctypes.Structure):
@@ -149,7 +149,7 @@ class Solver:
                  factor_prec="fp64", krylov="fp64", formulation="transformed", restart=30,
                  max_iter=3000, shift=None, stream=None, timing=False, sweep="auto",
                  ordering="natural", partitions=0, partition=None, stage_jacobians=False, spin_limit=0,
-                 kernel_options=None):
+                 kernel_options=None, orthogonalization="mgs"):
         lib = load()
         self._lib = lib
         self.s, self.T, self.m = int(s), int(T), int(m)
@@ -174,6 +174,7 @@ class Solver:
         opt.partitions = int(partitions)
         opt.stage_jacobians = 1 if stage_jacobians else 0
         opt.spin_limit = int(spin_limit)
+        opt.orthogonalization = {"mgs": 0, "cgs2": 1}[orthogonalization]
         self._part = None
         if partition is not None:
             self._part = np.ascontiguousarray(partition, dtype=np.int32)

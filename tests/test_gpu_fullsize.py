@@ -93,13 +93,13 @@ def test_c1_operator_full_size(c1, c1_ref, c1_dev):
 
 
 @pytest.mark.parametrize("dt", [0.01, 0.1, 1.0])
-@pytest.mark.parametrize("fprec,krylov", VARIANTS)
-def test_c1_solve_full_size(c1, c1_ref, c1_tight, c1_dev, dt, fprec, krylov):
+@pytest.mark.parametrize("fprec,krylov,ortho", [v + ("mgs",) for v in VARIANTS] + [("fp32", "df64", "cgs2")])
+def test_c1_solve_full_size(c1, c1_ref, c1_tight, c1_dev, dt, fprec, krylov, ortho):
     irk = _irk()
     P = c1
     rp, ci, J, M, R = c1_dev
     with irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec=fprec, krylov=krylov,
-                    ordering="multicolor") as S:
+                    ordering="multicolor", orthogonalization=ortho) as S:
         W, it, rr, rc = S.solve(R, dt, rtol=1e-8)
         fused = S.stats()["factor_fused_levels"]
     assert rc == 0 and rr <= 1e-8
@@ -130,13 +130,13 @@ def c2_tight(c2, c2_ref):
     return c2_ref.solve(c2.R, 0.1, rtol=1e-12)["x"]
 
 
-@pytest.mark.parametrize("fprec", ["fp32", "bf16"])
-def test_c2_full_size(c2, c2_ref, c2_tight, fprec):
+@pytest.mark.parametrize("fprec,ortho", [("fp32", "mgs"), ("bf16", "mgs"), ("fp32", "cgs2")])
+def test_c2_full_size(c2, c2_ref, c2_tight, fprec, ortho):
     irk = _irk()
     P = c2
     with irk.Solver(P.s, P.T, P.m, dev(P.row_ptr), dev(P.col_idx), dev(P.J), dev(P.M), precond="uncoupled",
-                    factor_prec=fprec, krylov="df64", ordering="multicolor") as S:
-        if fprec == "fp32":
+                    factor_prec=fprec, krylov="df64", ordering="multicolor", orthogonalization=ortho) as S:
+        if fprec == "fp32" and ortho == "mgs":
             X = np.random.default_rng(3).standard_normal(P.s * P.T * P.m)
             assert rel(S.apply_operator(dev(X), 0.1), c2_ref.apply(X, 0.1)) <= 1e-13
         W, it, rr, rc = S.solve(dev(P.R), 0.1, rtol=1e-8)
