@@ -469,6 +469,10 @@ typedef struct {
                                application where the element order allows it
                                (see irk_stats.sweep_two_colour); 0: the level
                                sweeps */
+    int sweep_compiled_levels; /* 1 (default): level sweeps of binary32 factors
+                               with double-float Krylov vectors by kernels
+                               compiled for block sizes 12/20/24/40/50; 0: the
+                               generic level kernels */
     int sweep_shared_upper; /* 1 (default): backward sweeps read each upper
                                block once for all stages where no factor update
                                reaches the upper blocks; 0: once per stage */

@@ -870,6 +870,7 @@ void irk_default_kernel_options(irk_kernel_options *ko) {
     if (!ko) return;
     ko->matvec_variant = -1;
     ko->sweep_two_colour = 1;
+    ko->sweep_compiled_levels = 1;
     ko->sweep_shared_upper = 1;
     ko->factor_fused = 2;
     ko->factor_gj_rows = 1;
@@ -882,6 +883,7 @@ int irk_set_kernel_options(irk_ctx *c, const irk_kernel_options *ko) {
     if (!c || !ko) return IRK_ERR_INVALID;
     if (ko->matvec_variant < -1 || ko->matvec_variant >= irk_matvec_variants() || ko->sweep_two_colour < 0 ||
         ko->sweep_two_colour > 1 || ko->sweep_shared_upper < 0 || ko->sweep_shared_upper > 1 ||
+        ko->sweep_compiled_levels < 0 || ko->sweep_compiled_levels > 1 ||
         ko->factor_fused < 0 || ko->factor_fused > 2 || ko->factor_gj_rows < 0 || ko->factor_gj_rows > 1 ||
         (ko->factor_gj_threads != 0 && (ko->factor_gj_threads < 32 || ko->factor_gj_threads > 256)) ||
         ko->factor_gj_split_min < 0 || ko->arnoldi_form < 0 || ko->arnoldi_form > 2)

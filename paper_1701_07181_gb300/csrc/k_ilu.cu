@@ -1441,6 +1441,39 @@ __global__ void __launch_bounds__(256) k_sweep_fd(const int *rows, int nrows, co
     }
 }
 
+// Forward level sweep with the block size at compile time (levels after the
+// first in a multicolour order): y_R = v_R - sum_p L_p y_col, a group of
+// B / RW threads per row, RW rows per thread, block_col_dot's arithmetic per
+// row (bitwise the generic k_sweep_fwd).
+template <class AR, class F, int B, int RW>
+__global__ void __launch_bounds__(256) k_sweep_fl(const int *rows, int nrows, const int *rp, const int *ci,
+                                                  const int *voff, const F *vals, const vec8 *v, float *y) {
+    constexpr int GT = B / RW, G = 256 / GT;
+    constexpr long long BB = (long long)B * B;
+    const int g = threadIdx.x / GT, a0 = (threadIdx.x - g * GT) * RW;
+    const int idx = blockIdx.x * G + g;
+    if (g >= G || idx >= nrows) return;
+    const int R = rows[idx];
+    float acc[RW];
+#pragma unroll
+    for (int r = 0; r < RW; ++r) acc[r] = CT<float>::template from_vec<AR>(AR::ld(v + voff[R] + a0 + r));
+    for (int p = rp[R]; p < rp[R + 1]; ++p) {
+        const int col = ci[p];
+        if (col >= R) break;
+        const float *yc = y + voff[col];  // rows of earlier levels (earlier launches)
+        float d[RW];
+        block_rows_dot<F, B, RW>(d, vals + p * BB + a0, [&](int c, float &x0, float &x1) {
+            const float2 f = __ldg(reinterpret_cast<const float2 *>(yc + c));
+            x0 = f.x;
+            x1 = f.y;
+        });
+#pragma unroll
+        for (int r = 0; r < RW; ++r) acc[r] -= d[r];
+    }
+#pragma unroll
+    for (int r = 0; r < RW; ++r) y[voff[R] + a0 + r] = acc[r];
+}
+
 template <class C, class F, int B, class XF>
 __device__ __forceinline__ C block_col_dot_b(const F *Bp, XF x) {
     C bv[B];
@@ -1456,8 +1489,10 @@ __device__ __forceinline__ C block_col_dot_b(const F *Bp, XF x) {
 }
 
 // K2 with the upper blocks shared by the S stages (-dt J_ij for every stage):
-// one group per first-colour element, each upper block read once.
-template <class AR, class C, class F, int S, int B>
+// one group per first-colour element, each upper block read once.  FY: the
+// row's starting value is its forward result y_R (a backward level of a
+// multicolour order) instead of v_R (the first colour of two, where y = v).
+template <class AR, class C, class F, int S, int B, bool FY = false>
 __global__ void __launch_bounds__(256) k_sweep_bu(const int *rows0, int nrows, int T, const int *rp, const int *ci,
                                                   const int *voff, const F *vals, const F *dinv, const vec8 *v,
                                                   C *y, vec8 *z) {
@@ -1472,7 +1507,8 @@ __global__ void __launch_bounds__(256) k_sweep_bu(const int *rows0, int nrows, i
         R0 = rows0[idx];
         C acc[S];
 #pragma unroll
-        for (int k = 0; k < S; ++k) acc[k] = CT<C>::template from_vec<AR>(AR::ld(v + voff[k * T + R0] + a));
+        for (int k = 0; k < S; ++k)
+            acc[k] = FY ? y[voff[k * T + R0] + a] : CT<C>::template from_vec<AR>(AR::ld(v + voff[k * T + R0] + a));
         for (int p = rp[R0 + 1] - 1; p >= rp[R0]; --p) {
             const int col = ci[p];
             if (col <= R0) break;
@@ -2371,6 +2407,56 @@ static bool apply_two_colour(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, 
     return true;
 }
 
+// Level sweeps with the block size at compile time (binary32 compute,
+// double-float vectors): the first forward level (rows without lower
+// entries: y = v) by the generic kernel, the others by k_sweep_fl, every
+// backward level by k_sweep_bu starting from y.  The same arithmetic as the
+// generic level kernels, so the same bits.
+template <class AR, class C, class F, int B>
+static bool apply_levels_b(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv) {
+    PcSystem &P = c->pc;
+    if (P.b != B) return false;
+    constexpr int RW = (B % 4 == 0) ? 4 : 2;
+    constexpr int G = 256 / (B / RW);
+    const int threads = (G * (B / RW) + 31) / 32 * 32;
+    constexpr int G1 = 256 / B;
+    const int threads1 = (G1 * B + 31) / 32 * 32;
+    C *y = (C *)P.d_y;
+    const int nlo = (int)P.lo_ptr.size() - 1;
+    int tm = tmark_begin(c);
+    for (int l = 0; l < nlo; ++l) {
+        const int n = P.lo_ptr[l + 1] - P.lo_ptr[l];
+        if (n <= 0) continue;
+        if (l == 0) {
+            const int groups = std::max(1, 256 / B);
+            k_sweep_fwd<AR, C, F><<<(n + groups - 1) / groups, (groups * B + 31) / 32 * 32, 0, c->stream>>>(
+                P.d_lo_rows + P.lo_ptr[l], n, B, P.d_rp, P.d_ci, P.d_voff, vals, v, y);
+        } else {
+            k_sweep_fl<AR, F, B, RW><<<(n + G - 1) / G, threads, 0, c->stream>>>(
+                P.d_lo_rows + P.lo_ptr[l], n, P.d_rp, P.d_ci, P.d_voff, vals, v, y);
+        }
+        c->launches++;
+    }
+    tmark_end(c, tm, 6);
+    tm = tmark_begin(c);
+    const int s = c->s;
+    const bool shared = P.shared_upper && s >= 2 && s <= 4 && c->ko.sweep_shared_upper;
+    auto kern = !shared ? k_sweep_bu<AR, C, F, 1, B, true>
+                        : (s == 2 ? k_sweep_bu<AR, C, F, 2, B, true>
+                                  : (s == 3 ? k_sweep_bu<AR, C, F, 3, B, true> : k_sweep_bu<AR, C, F, 4, B, true>));
+    const std::vector<int> &up = shared ? P.up0_ptr : P.up_ptr;
+    const int *rows = shared ? P.d_up0_rows : P.d_up_rows;
+    for (int l = 0; l + 1 < (int)up.size(); ++l) {
+        const int n = up[l + 1] - up[l];
+        if (n <= 0) continue;
+        kern<<<(n + G1 - 1) / G1, threads1, 0, c->stream>>>(rows + up[l], n, c->T, P.d_rp, P.d_ci, P.d_voff, vals,
+                                                          dinv, v, y, z);
+        c->launches++;
+    }
+    tmark_end(c, tm, 7);
+    return true;
+}
+
 template <class AR, class C, class F>
 static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F *dinv) {
     PcSystem &P = c->pc;
@@ -2384,6 +2470,11 @@ static int apply_impl(irk_ctx *c, const vec8 *v, vec8 *z, const F *vals, const F
              apply_two_colour<AR, C, F, 24>(c, v, z, vals, dinv) ||
              apply_two_colour<AR, C, F, 20>(c, v, z, vals, dinv) ||
              apply_two_colour<AR, C, F, 12>(c, v, z, vals, dinv)))
+            return cuda_status(cudaGetLastError());
+        if (c->ko.sweep_compiled_levels &&
+            (apply_levels_b<AR, C, F, 40>(c, v, z, vals, dinv) || apply_levels_b<AR, C, F, 50>(c, v, z, vals, dinv) ||
+             apply_levels_b<AR, C, F, 24>(c, v, z, vals, dinv) || apply_levels_b<AR, C, F, 20>(c, v, z, vals, dinv) ||
+             apply_levels_b<AR, C, F, 12>(c, v, z, vals, dinv)))
             return cuda_status(cudaGetLastError());
     }
     const int groups = std::max(1, 256 / b);

@@ -46,7 +46,7 @@ class Options(ctypes.Structure):
 
 class KernelOptions(ctypes.Structure):
     _fields_ = [("matvec_variant", ctypes.c_int), ("sweep_two_colour", ctypes.c_int),
-                ("sweep_shared_upper", ctypes.c_int), ("factor_fused", ctypes.c_int),
+                ("sweep_compiled_levels", ctypes.c_int), ("sweep_shared_upper", ctypes.c_int), ("factor_fused", ctypes.c_int),
                 ("factor_gj_rows", ctypes.c_int), ("factor_gj_threads", ctypes.c_int),
                 ("factor_gj_split_min", ctypes.c_int), ("arnoldi_form", ctypes.c_int)]
 
