@@ -8,7 +8,7 @@ m = 40, s = 3: inputs still larger than L2) with the benchmark's options
 (FP32 factors, double-float Krylov vectors, two-colour ordering), so DRAM
 counters per launch can be scaled to the full workload by the element count.
 
-Usage: ``python profile_case.py [--nx 60 --ny 60 --m 40 --s 3 --solves 2]``
+Usage: ``python profile_case.py [--nx 60 --ny 60 --m 40 --s 3 --solves 2 --matvec-variant V]``
 """
 from __future__ import annotations
 
@@ -29,6 +29,8 @@ def main(argv=None):
     ap.add_argument("--s", type=int, default=3)
     ap.add_argument("--solves", type=int, default=2)
     ap.add_argument("--ordering", default="multicolor")
+    ap.add_argument("--matvec-variant", type=int, default=-1,
+                    help="pin the operator-product launch variant (-1: autotuned)")
     args = ap.parse_args(argv)
     import torch
 
@@ -39,7 +41,8 @@ def main(argv=None):
         return torch.as_tensor(np.ascontiguousarray(a)).cuda()
 
     with irk.Solver(P.s, P.T, P.m, dev(P.row_ptr), dev(P.col_idx), dev(P.J), dev(P.M), factor_prec="fp32",
-                    krylov="df64", timing=True, ordering=args.ordering) as S:
+                    krylov="df64", timing=True, ordering=args.ordering,
+                    kernel_options={"matvec_variant": args.matvec_variant}) as S:
         R = dev(P.R)
         for k in range(args.solves):
             W, it, rr, rc = S.solve(R, 0.1 * (k + 1))
