@@ -431,8 +431,10 @@ typedef struct {
      * warp streams 8-column chunks of the blocks and the matching stage
      * values into shared memory, the other warps compute from there), 12
      * and 13 the TMA-fed kernel with 16-column chunks and two units in
-     * flight, and with 8-column chunks and three; -1 before the first
-     * product.  irk_kernel_options.matvec_variant pins the variant.  Every variant
+     * flight, and with 8-column chunks and three, 14-16 the TMA-fed kernel
+     * with two rows per consumer thread in packed two-lane binary32
+     * arithmetic and about 128 consumer threads per CTA ((8, 3), (8, 2) and
+     * (10, 2) chunk columns and units); -1 before the first product.  irk_kernel_options.matvec_variant pins the variant.  Every variant
      * gives the same result bit for bit. */
     int matvec_variant;
     /* with irk_options.timing = 1: device time of the kernels of the last
@@ -463,7 +465,7 @@ IRK_API int irk_get_stats(const irk_ctx *ctx, irk_stats *out);
  * gives the same result bit for bit except where noted. */
 typedef struct {
     int matvec_variant;     /* -1 (default): operator-product launch variant
-                               autotuned per (m, s, arithmetic); 0..13 pin one
+                               autotuned per (m, s, arithmetic); 0..16 pin one
                                (see irk_stats.matvec_variant) */
     int sweep_two_colour;   /* 1 (default): the two-launch preconditioner
                                application where the element order allows it

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libirk_gb300.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["api.cu", "k_matvec.cu", "k_krylov.cu", "k_ilu.cu", "group.cu", "dirk.cu"]
+SOURCES = ["api.cu", "k_matvec.cu", "k_matvec_tp.cu", "k_krylov.cu", "k_ilu.cu", "group.cu", "dirk.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 

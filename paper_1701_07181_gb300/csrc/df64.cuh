@@ -169,3 +169,95 @@ __device__ __forceinline__ df64 df_div(df64 a, df64 b) {
     fast_two_sum(q1, q2, h, l);
     return df_make(h, l);
 }
+
+// ---------------------------------------------------------------------------
+// Two accumulators in one packed register pair.  The sm_100 family executes
+// add/sub/mul/fma on two binary32 lanes per instruction (PTX .f32x2), each
+// lane rounded as the scalar operation: the FP32 pipe does the same work,
+// but one instruction issue covers both lanes, which leaves issue slots to
+// the loads and the bookkeeping of an issue-bound loop.  df_acc2 holds two
+// independent Dot2 accumulators (e.g. two rows of a block); every lane sees
+// exactly the operations of df_acc_fma / df_acc_fma_f / df_acc_renorm above,
+// so the results are theirs bit for bit.  A subtraction a - b is written as
+// a - b or as a + (-b) where that saves a negation; binary32 negation and
+// round-to-nearest are symmetric, so both give the scalar result exactly.
+typedef unsigned long long f32x2;
+
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_sub(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+
+struct df_acc2 {
+    f32x2 s, c;
+};
+
+__device__ __forceinline__ df_acc2 df_acc2_zero() {
+    df_acc2 a;
+    a.s = f2_pack(0.f, 0.f);
+    a.c = a.s;
+    return a;
+}
+
+// Lane k: acc_k += (bh_k + bl_k) * y for one binary32 y (df_acc_fma_f with
+// x = (bh_k, bl_k)); yn = -y.
+__device__ __forceinline__ void df_acc2_fma_f(df_acc2 &acc, f32x2 bh, f32x2 bl, f32x2 y, f32x2 yn) {
+    const f32x2 pn = f2_mul(bh, yn);          // -p, p = bh y
+    const f32x2 e = f2_fma(bh, y, pn);        // bh y - p, exact
+    const f32x2 s = f2_sub(acc.s, pn);        // TwoSum(acc.s, p): s = acc.s + p
+    const f32x2 bb = f2_sub(s, acc.s);
+    const f32x2 t = f2_sub(f2_sub(acc.s, f2_sub(s, bb)), f2_add(pn, bb));  // (acc.s - (s - bb)) + (p - bb)
+    const f32x2 c = f2_fma(bl, y, acc.c);
+    acc.s = s;
+    acc.c = f2_add(c, f2_add(t, e));
+}
+
+// Lane k: acc_k += (bh_k + bl_k) * (yh + yl) (df_acc_fma); yhn = -yh.
+__device__ __forceinline__ void df_acc2_fma(df_acc2 &acc, f32x2 bh, f32x2 bl, f32x2 yh, f32x2 yhn, f32x2 yl) {
+    const f32x2 pn = f2_mul(bh, yhn);
+    const f32x2 e = f2_fma(bh, yh, pn);
+    const f32x2 s = f2_sub(acc.s, pn);
+    const f32x2 bb = f2_sub(s, acc.s);
+    const f32x2 t = f2_sub(f2_sub(acc.s, f2_sub(s, bb)), f2_add(pn, bb));
+    f32x2 c = f2_fma(bh, yl, acc.c);
+    c = f2_fma(bl, yh, c);
+    acc.s = s;
+    acc.c = f2_add(c, f2_add(t, e));
+}
+
+// df_acc_renorm on both lanes
+__device__ __forceinline__ void df_acc2_renorm(df_acc2 &acc) {
+    const f32x2 s = f2_add(acc.s, acc.c);
+    acc.c = f2_sub(acc.c, f2_sub(s, acc.s));
+    acc.s = s;
+}
+
+// lane 0 and lane 1 as scalar accumulators
+__device__ __forceinline__ void df_acc2_split(df_acc2 a, df_acc &l0, df_acc &l1) {
+    f2_unpack(a.s, l0.s, l1.s);
+    f2_unpack(a.c, l0.c, l1.c);
+}

@@ -25,29 +25,12 @@
 #include <type_traits>
 
 #include "arith.cuh"
+#include "matvec.cuh"
 #include "tma.cuh"
 
+using namespace irk_mv;
+
 namespace {
-
-struct MatvecParams {
-    int T, m, form, mode;
-    int xf32;  // 1: every x value is binary32 (double-float with a zero low word)
-    const int *rp, *ci;
-    const vec8 *J, *M, *x, *rhs;
-    vec8 *y;
-    KCoef C[IRK_MAX_S * IRK_MAX_S];  // A^{-1} (transformed) or A (untransformed)
-    KCoef mdt;                       // -dt
-    // one Jacobian per stage (k_matvec_ps): J_k = J + k * jstride; A for the
-    // untransformed combination sum_l a_kl x_l
-    long long jstride;
-    KCoef Acomb[IRK_MAX_S * IRK_MAX_S];
-};
-
-// Columns after which every double-float accumulator of the operator product
-// folds its error term into its sum (df_acc_renorm): every eighth column of a
-// block and its last one.  All launch variants fold at the same columns, so
-// they stay bitwise identical.
-__device__ __forceinline__ bool fold_after(int c, int m) { return (c & 7) == 7 || c == m - 1; }
 
 // dst[l] += sum_c B[c][a] x[l][c] for one column-major block (thread's row a
 // pre-applied to B).  Chunks of CH columns: all loads of a chunk are issued
@@ -71,52 +54,6 @@ __device__ __forceinline__ void accum_block(typename AR::acc (&dst)[S], const ve
 #pragma unroll
                 for (int l = 0; l < S; ++l) AR::renorm(dst[l]);
         }
-    }
-}
-
-// Mixes the per-stage sums of row i (t_l = sum_j J_ij x_{l,j},
-// z_l = M_i x_{l,i}) into the s outputs of thread row a and stores them
-// (mode 1: rhs - y).  IRK_FORM_JACOBIAN: y_k = t_k (the Jacobian alone).
-template <class AR, int S>
-__device__ __forceinline__ void store_row(const MatvecParams &P, long long i, int a, const typename AR::acc (&t)[S],
-                                          const typename AR::acc (&z)[S]) {
-    typedef typename AR::val val;
-    typedef typename AR::acc acc;
-    const int m = P.m;
-    const long long sm = (long long)S * m;
-    val tv[S], zv[S];
-#pragma unroll
-    for (int l = 0; l < S; ++l) {
-        tv[l] = AR::value(t[l]);
-        zv[l] = AR::value(z[l]);
-    }
-    const val mdt = AR::coef(P.mdt.d, P.mdt.hi, P.mdt.lo);
-#pragma unroll
-    for (int k = 0; k < S; ++k) {
-        acc o = AR::zero();
-        if (P.form == IRK_FORM_JACOBIAN) {
-            AR::add_to(o, tv[k]);
-        } else if (P.form == IRK_TRANSFORMED) {
-#pragma unroll
-            for (int l = 0; l < S; ++l) {
-                const KCoef &cc = P.C[k * S + l];
-                AR::fma(o, AR::coef(cc.d, cc.hi, cc.lo), zv[l]);
-            }
-            AR::fma(o, mdt, tv[k]);
-        } else {
-            AR::add_to(o, zv[k]);
-            acc q = AR::zero();
-#pragma unroll
-            for (int l = 0; l < S; ++l) {
-                const KCoef &cc = P.C[k * S + l];
-                AR::fma(q, AR::coef(cc.d, cc.hi, cc.lo), tv[l]);
-            }
-            AR::fma(o, mdt, AR::value(q));
-        }
-        val out = AR::value(o);
-        vec8 *dst = P.y + i * sm + k * m + a;
-        if (P.mode == 1) out = AR::sub(AR::ld(P.rhs + i * sm + k * m + a), out);
-        AR::st(dst, out);
     }
 }
 
@@ -189,14 +126,6 @@ __device__ __forceinline__ df64 ld_stream(const vec8 *p) {
     asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(h), "=f"(l) : "l"(p));
     return df_make(h, l);
 }
-
-// Element rows per CTA of the look-ahead kernel: as many as fill whole warps
-// (G B a multiple of 32) within 256 threads, else 256 / B.
-__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
-__host__ __device__ constexpr int sp_groups(int B) {
-    return (B * 32 / gcd_c(B, 32) <= 256) ? (256 / (B * 32 / gcd_c(B, 32))) * (32 / gcd_c(B, 32)) : 256 / B;
-}
-__host__ __device__ constexpr int sp_threads(int B) { return (sp_groups(B) * B + 31) / 32 * 32; }
 
 // accum_block_b with the block loads one chunk ahead: chunk c + CH's
 // columns are requested before chunk c's arithmetic, so the loads overlap a
@@ -482,189 +411,6 @@ __device__ __forceinline__ void accum_block_smem(typename AR::acc (&dst)[S], con
     }
 }
 
-// ---------------------------------------------------------------------------
-// TMA-fed variant with the block size at compile time (double-float).  A CTA
-// holds G row groups of B consumer threads (whole warps) and one producer
-// warp; lane g of the producer warp streams group g's work as units of CK
-// block columns, one bulk copy each (CK B entries, contiguous in the
-// column-major layout), into a ring of NU units per group, and with the
-// first unit of every block one more copy of the s B stage values of the
-// block's neighbour into a ring of NX stage-value slots; each unit completes
-// on its "full" mbarrier.  The consumers read only shared memory (the HBM
-// stream and the neighbours' stage values arrive ahead of them without
-// holding registers) and release a unit on its "empty" mbarrier (B
-// arrivals).  Refilling a unit's slot waits for the unit NU places earlier,
-// which lies past the last unit of the block NX places earlier, so a
-// stage-value slot is refilled only after its block is done (NX below).
-// Rows: group g of CTA b takes rows (b + t gridDim.x) G + g, t = 0, 1, ...
-// Every accumulator sees the columns in ascending order and folds after the
-// same columns as every other variant: the result is theirs, bit for bit.
-// Waits are bounded; on a timeout the kernel records IRK_DEV_ERR_TIMEOUT,
-// the producer stops issuing and waits for its copies in flight, and every
-// thread leaves.
-template <int S, int B, int CK, int NU>
-struct TpShape {
-    static constexpr int G = sp_groups(B);               // row groups per CTA
-    static constexpr int CONS = (G * B + 31) / 32 * 32;  // consumer threads (whole warps)
-    static constexpr int THREADS = CONS + 32;            // and the producer warp
-    static constexpr int UPB = (B + CK - 1) / CK;        // units per block
-    static constexpr int NX = 1 + (NU - 1 + UPB - 1) / UPB;  // stage-value slots per group
-    static constexpr int UNIT = CK * B * 8;              // a multiple of 16 for even B
-    static constexpr int XSLOT = S * B * 8;
-    static constexpr int HEADER = ((2 * NU * G * 8 + 16 + 127) / 128) * 128;
-    static constexpr int GROUP = NU * UNIT + NX * XSLOT;  // a multiple of 16
-    static constexpr int SMEM = HEADER + G * GROUP;
-};
-
-// acc[l] += sum over NC columns (from c0) of B_entry * x_l (thread row a),
-// two columns at a time; the fold points (every eighth column, the block's
-// last) are the second column of a pair (B even)
-template <int S, int B, bool XF, int NC>
-__device__ __forceinline__ void tp_consume(df_acc (&acc)[S], const unsigned char *unit, const float *X, int c0,
-                                           int a) {
-    const float2 *Jc = reinterpret_cast<const float2 *>(unit);
-#pragma unroll
-    for (int c = 0; c < NC; c += 2) {
-        const float2 b0 = Jc[c * B + a], b1 = Jc[(c + 1) * B + a];
-#pragma unroll
-        for (int l = 0; l < S; ++l) {
-            const float4 xv = *reinterpret_cast<const float4 *>(X + 2 * (l * B + c0 + c));
-            if (XF) {
-                df_acc_fma_f(acc[l], df_make(b0.x, b0.y), xv.x);
-                df_acc_fma_f(acc[l], df_make(b1.x, b1.y), xv.z);
-            } else {
-                df_acc_fma(acc[l], df_make(b0.x, b0.y), df_make(xv.x, xv.y));
-                df_acc_fma(acc[l], df_make(b1.x, b1.y), df_make(xv.z, xv.w));
-            }
-        }
-        if (fold_after(c0 + c + 1, B))
-#pragma unroll
-            for (int l = 0; l < S; ++l) df_acc_renorm(acc[l]);
-    }
-}
-
-// One block's units into acc; blk counts the group's blocks (its stage-value
-// slot); false on a timeout.
-template <int S, int B, bool XF, int CK, int NU>
-__device__ __forceinline__ bool tp_block(df_acc (&acc)[S], const unsigned char *gr, unsigned long long *fb,
-                                         unsigned long long *eb, int &used, int blk, int a, int *err,
-                                         volatile int *abort_flag) {
-    using SH = TpShape<S, B, CK, NU>;
-    constexpr int NCH = SH::UPB;
-    constexpr int LAST = B - (NCH - 1) * CK;
-    const float *X = reinterpret_cast<const float *>(gr + NU * SH::UNIT + (blk % SH::NX) * SH::XSLOT);
-    // one copy of the unit's code (not unrolled over the chunks: the
-    // unrolled form overflows the instruction cache)
-#pragma unroll 1
-    for (int ch = 0; ch < NCH; ++ch) {
-        const int q = used % NU;
-        if (!mbar_wait(fb + q, (unsigned)(used / NU) & 1u)) {
-            atomicOr(err, IRK_DEV_ERR_TIMEOUT);
-            *abort_flag = 1;
-            return false;
-        }
-        const unsigned char *unit = gr + q * SH::UNIT;
-        const int c0 = ch * CK;
-        if (LAST == CK || ch < NCH - 1)
-            tp_consume<S, B, XF, CK>(acc, unit, X, c0, a);
-        else
-            tp_consume<S, B, XF, LAST>(acc, unit, X, c0, a);
-        mbar_arrive(eb + q);
-        ++used;
-    }
-    return true;
-}
-
-template <int S, int B, bool XF, int CK, int NU>
-__global__ void __launch_bounds__(TpShape<S, B, CK, NU>::THREADS,
-                                  S <= 3 ? (XF ? 2048 : 1536) / TpShape<S, B, CK, NU>::THREADS : 1)
-    k_matvec_tp(MatvecParams P, int *err) {
-    using SH = TpShape<S, B, CK, NU>;
-    constexpr int G = SH::G;
-    constexpr long long BB = (long long)B * B, SB = (long long)S * B;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw);  // [G][NU]
-    unsigned long long *empty = full + G * NU;                                   // [G][NU]
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem_raw + 2 * NU * G * 8);
-    unsigned char *ring = smem_raw + SH::HEADER;
-    const int tid = threadIdx.x;
-    if (tid == 0) {
-        for (int q = 0; q < G * NU; ++q) {
-            mbar_init_n(full + q, 1);
-            mbar_init_n(empty + q, B);
-        }
-        *abort_flag = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    __syncthreads();
-    const int rstride = gridDim.x * G;  // T < 2^31
-    if (tid >= SH::CONS) {
-        // producer: lane g streams group g's units (one thread per group: a
-        // single thread serving every group in turn with non-blocking tests
-        // measured slower, 0.29 -> 0.33 ms on the 20000-triangle workload)
-        const int g = tid - SH::CONS;
-        if (g >= G) return;
-        unsigned long long *fb = full + g * NU, *eb = empty + g * NU;
-        unsigned char *gr = ring + g * SH::GROUP;
-        int issued = 0, nblk = 0;
-        bool ok = true;
-        for (int i = blockIdx.x * G + g; i < P.T && ok; i += rstride) {
-            const int p0 = P.rp[i], p1 = P.rp[i + 1];
-            const int pend = P.form != IRK_FORM_JACOBIAN ? p1 : p1 - 1;  // p == p1: the mass block
-            for (int p = p0; p <= pend && ok; ++p, ++nblk) {
-                const vec8 *blk = p < p1 ? P.J + (long long)p * BB : P.M + (long long)i * BB;
-                const vec8 *xs = P.x + (long long)(p < p1 ? P.ci[p] : i) * SB;
-                for (int c0 = 0; c0 < B; c0 += CK) {
-                    const int nc = B - c0 < CK ? B - c0 : CK;
-                    const int q = issued % NU;
-                    if (issued >= NU && !mbar_wait(eb + q, (unsigned)((issued / NU) - 1) & 1u)) {
-                        atomicOr(err, IRK_DEV_ERR_TIMEOUT);
-                        *abort_flag = 1;
-                        ok = false;
-                        break;
-                    }
-                    if (*abort_flag) {
-                        ok = false;
-                        break;
-                    }
-                    const unsigned jb = (unsigned)(nc * B * 8);
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    if (c0 == 0) {
-                        mbar_expect_arrive(fb + q, jb + (unsigned)SH::XSLOT);
-                        tma_load_1d(gr + NU * SH::UNIT + (nblk % SH::NX) * SH::XSLOT, xs, (unsigned)SH::XSLOT, fb + q);
-                    } else {
-                        mbar_expect_arrive(fb + q, jb);
-                    }
-                    tma_load_1d(gr + q * SH::UNIT, blk + (long long)c0 * B, jb, fb + q);
-                    ++issued;
-                }
-            }
-        }
-        // no copy into this CTA's shared memory may be in flight when it exits
-        for (int u = issued > NU ? issued - NU : 0; u < issued; ++u) mbar_wait(fb + u % NU, (unsigned)(u / NU) & 1u);
-        return;
-    }
-    const int g = tid / B, a = tid - g * B;
-    if (g >= G) return;  // lanes past the last group
-    unsigned long long *fb = full + g * NU, *eb = empty + g * NU;
-    const unsigned char *gr = ring + g * SH::GROUP;
-    int used = 0, nblk = 0;
-    for (int i = blockIdx.x * G + g; i < P.T; i += rstride) {
-        df_acc t[S], z[S];
-#pragma unroll
-        for (int l = 0; l < S; ++l) {
-            t[l] = df_acc_zero();
-            z[l] = df_acc_zero();
-        }
-        const int p0 = P.rp[i], p1 = P.rp[i + 1];
-        for (int p = p0; p < p1; ++p)
-            if (!tp_block<S, B, XF, CK, NU>(t, gr, fb, eb, used, nblk++, a, err, abort_flag)) return;
-        if (P.form != IRK_FORM_JACOBIAN && !tp_block<S, B, XF, CK, NU>(z, gr, fb, eb, used, nblk++, a, err, abort_flag))
-            return;
-        store_row<ArDF, S>(P, i, a, t, z);
-    }
-}
-
 #define IRK_MV_MAX_STAGES 4
 #define IRK_MV_HEADER 256  // bytes before the slots: barriers, timeout words, producer cursors
 
@@ -920,37 +666,25 @@ int grid_for(long long work, int threads) {
 // 24, 40 or 50; four columns of loads in flight).  8: k_matvec_rb (the
 // same, register-blocked: four rows per thread, two for m = 50).  9:
 // k_matvec_b with eight columns in flight.  10: k_matvec_sp (k_matvec_b with
-// the block loads one chunk ahead).  11: k_matvec_tp (TMA-fed: a producer
-// warp streams column chunks and stage values into shared memory).  Picked per (m, s, arithmetic) by the autotuner below; all
-// give identical results; a variant that does not apply runs variant 0.
+// the block loads one chunk ahead).  11-13: k_matvec_tp (TMA-fed: a
+// producer warp streams column chunks and stage values into shared memory)
+// with (columns per unit, units in the ring) = (8, 4), (16, 2), (8, 3).
+// 14-16: k_matvec_tp with two rows per consumer thread in packed two-lane
+// arithmetic and about 128 consumer threads per CTA, (8, 3), (8, 2), (10, 2).  Picked per (m, s, arithmetic) by the
+// autotuner below; all give identical results; a variant that does not
+// apply runs variant 0.
 struct MvVariant {
     int ch, threads;  // k_matvec / k_matvec_b
     int ns, per_sm;   // k_matvec_pipe (ns > 0)
-    int fixed;        // 1: k_matvec_b, 2: k_matvec_rb, 3: k_matvec_b with CH = 8, 4: k_matvec_sp, 5: k_matvec_tp
+    int fixed;        // 1: k_matvec_b, 2: k_matvec_rb, 3: k_matvec_b with CH = 8, 4: k_matvec_sp,
+                      // 5-7: k_matvec_tp, 8-10: k_matvec_tp with two rows per thread
 };
 const MvVariant kMvVariants[] = {{8, 256, 0, 0, 0}, {4, 256, 0, 0, 0}, {2, 256, 0, 0, 0}, {4, 128, 0, 0, 0},
                                  {0, 0, 2, 1, 0},   {0, 0, 3, 1, 0},   {0, 0, 2, 2, 0},   {4, 256, 0, 0, 1},
                                  {2, 256, 0, 0, 2}, {8, 256, 0, 0, 3}, {4, 256, 0, 0, 4}, {0, 0, 0, 0, 5},
-                                 {0, 0, 0, 0, 6},   {0, 0, 0, 0, 7}};
-const int kNumMvVariants = 14;
-
-struct DevLimits {
-    int sms = 0, optin = 0, per_sm = 0;
-};
-DevLimits dev_limits() {
-    static std::mutex mu;
-    static DevLimits cached[64];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::lock_guard<std::mutex> g(mu);
-    DevLimits &L = cached[dev & 63];
-    if (L.sms == 0) {
-        cudaDeviceGetAttribute(&L.sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaDeviceGetAttribute(&L.optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        cudaDeviceGetAttribute(&L.per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-    }
-    return L;
-}
+                                 {0, 0, 0, 0, 6},   {0, 0, 0, 0, 7},   {0, 0, 0, 0, 8},   {0, 0, 0, 0, 9},
+                                 {0, 0, 0, 0, 10}};
+const int kNumMvVariants = 17;
 
 // Groups per CTA of a pipelined variant (0: not applicable).  Needs m even
 // (16-byte multiples for the bulk copies) and 16-byte aligned operands.
@@ -1019,41 +753,11 @@ bool run_matvec_sp(const MatvecParams &P, cudaStream_t st) {
     return true;
 }
 
-template <int S, int B, int CK, int NU>
-bool run_matvec_tp(const MatvecParams &P, int *err, cudaStream_t st) {
-    if (P.m != B) return false;
-    using SH = TpShape<S, B, CK, NU>;
-    static_assert(B % 2 == 0, "bulk copies need 16-byte multiples");
-    const void *kern = P.xf32 ? (const void *)k_matvec_tp<S, B, true, CK, NU>
-                              : (const void *)k_matvec_tp<S, B, false, CK, NU>;
-    if (irk_allow_max_smem(kern)) return false;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::THREADS, SH::SMEM) != cudaSuccess ||
-        per_sm <= 0)
-        return false;
-    const long long need = (P.T + SH::G - 1) / SH::G;
-    const long long grid = std::max(1LL, std::min<long long>(need, (long long)dev_limits().sms * per_sm));
-    if (P.xf32)
-        k_matvec_tp<S, B, true, CK, NU><<<(int)grid, SH::THREADS, SH::SMEM, st>>>(P, err);
-    else
-        k_matvec_tp<S, B, false, CK, NU><<<(int)grid, SH::THREADS, SH::SMEM, st>>>(P, err);
-    return true;
-}
-
-template <int S, int CK, int NU>
-bool run_matvec_tp_any(const MatvecParams &P, int *err, cudaStream_t st) {
-    return run_matvec_tp<S, 40, CK, NU>(P, err, st) || run_matvec_tp<S, 50, CK, NU>(P, err, st) ||
-           run_matvec_tp<S, 24, CK, NU>(P, err, st) || run_matvec_tp<S, 20, CK, NU>(P, err, st) ||
-           run_matvec_tp<S, 12, CK, NU>(P, err, st);
-}
-
 template <class AR, int S>
 bool run_matvec_fixed(const MatvecParams &P, int form, int *err, cudaStream_t st) {
     if constexpr (std::is_same<AR, ArDF>::value && S >= 2 && S <= 4) {
         if ((((uintptr_t)P.x | (uintptr_t)P.J | (uintptr_t)P.M) & 15) != 0) return false;
-        if (form == 5) return run_matvec_tp_any<S, 8, 4>(P, err, st);
-        if (form == 6) return run_matvec_tp_any<S, 16, 2>(P, err, st);
-        if (form == 7) return run_matvec_tp_any<S, 8, 3>(P, err, st);
+        if (form >= 5) return run_matvec_tp_form(P, S, form, err, st);
         if (form == 2)
             return run_matvec_rb<S, 40, 2>(P, st) || run_matvec_rb<S, 50, 1>(P, st) ||
                    run_matvec_rb<S, 24, 2>(P, st) || run_matvec_rb<S, 20, 2>(P, st) || run_matvec_rb<S, 12, 2>(P, st);
