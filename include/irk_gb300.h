@@ -433,8 +433,9 @@ typedef struct {
      * and 13 the TMA-fed kernel with 16-column chunks and two units in
      * flight, and with 8-column chunks and three, 14-16 the TMA-fed kernel
      * with two rows per consumer thread in packed two-lane binary32
-     * arithmetic and about 128 consumer threads per CTA ((8, 3), (8, 2) and
-     * (10, 2) chunk columns and units); -1 before the first product.  irk_kernel_options.matvec_variant pins the variant.  Every variant
+     * arithmetic and about 128 consumer threads per CTA ((8, 3) and (8, 2)
+     * chunk columns and units, and (8, 2) with registers capped for five
+     * CTAs per SM); -1 before the first product.  irk_kernel_options.matvec_variant pins the variant.  Every variant
      * gives the same result bit for bit. */
     int matvec_variant;
     /* with irk_options.timing = 1: device time of the kernels of the last

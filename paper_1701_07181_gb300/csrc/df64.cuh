@@ -223,10 +223,13 @@ __device__ __forceinline__ df_acc2 df_acc2_zero() {
     return a;
 }
 
+// Negation of both lanes (sign bits flipped: exact, on the integer pipe).
+__device__ __forceinline__ f32x2 f2_neg(f32x2 a) { return a ^ 0x8000000080000000ull; }
+
 // Lane k: acc_k += (bh_k + bl_k) * y for one binary32 y (df_acc_fma_f with
-// x = (bh_k, bl_k)); yn = -y.
-__device__ __forceinline__ void df_acc2_fma_f(df_acc2 &acc, f32x2 bh, f32x2 bl, f32x2 y, f32x2 yn) {
-    const f32x2 pn = f2_mul(bh, yn);          // -p, p = bh y
+// x = (bh_k, bl_k)); bhn = -bh.
+__device__ __forceinline__ void df_acc2_fma_f(df_acc2 &acc, f32x2 bh, f32x2 bhn, f32x2 bl, f32x2 y) {
+    const f32x2 pn = f2_mul(bhn, y);          // -p, p = bh y
     const f32x2 e = f2_fma(bh, y, pn);        // bh y - p, exact
     const f32x2 s = f2_sub(acc.s, pn);        // TwoSum(acc.s, p): s = acc.s + p
     const f32x2 bb = f2_sub(s, acc.s);
@@ -236,9 +239,9 @@ __device__ __forceinline__ void df_acc2_fma_f(df_acc2 &acc, f32x2 bh, f32x2 bl, 
     acc.c = f2_add(c, f2_add(t, e));
 }
 
-// Lane k: acc_k += (bh_k + bl_k) * (yh + yl) (df_acc_fma); yhn = -yh.
-__device__ __forceinline__ void df_acc2_fma(df_acc2 &acc, f32x2 bh, f32x2 bl, f32x2 yh, f32x2 yhn, f32x2 yl) {
-    const f32x2 pn = f2_mul(bh, yhn);
+// Lane k: acc_k += (bh_k + bl_k) * (yh + yl) (df_acc_fma); bhn = -bh.
+__device__ __forceinline__ void df_acc2_fma(df_acc2 &acc, f32x2 bh, f32x2 bhn, f32x2 bl, f32x2 yh, f32x2 yl) {
+    const f32x2 pn = f2_mul(bhn, yh);
     const f32x2 e = f2_fma(bh, yh, pn);
     const f32x2 s = f2_sub(acc.s, pn);
     const f32x2 bb = f2_sub(s, acc.s);

@@ -670,7 +670,8 @@ int grid_for(long long work, int threads) {
 // producer warp streams column chunks and stage values into shared memory)
 // with (columns per unit, units in the ring) = (8, 4), (16, 2), (8, 3).
 // 14-16: k_matvec_tp with two rows per consumer thread in packed two-lane
-// arithmetic and about 128 consumer threads per CTA, (8, 3), (8, 2), (10, 2).  Picked per (m, s, arithmetic) by the
+// arithmetic and about 128 consumer threads per CTA, (8, 3), (8, 2), and
+// (8, 2) with registers capped for five CTAs per SM.  Picked per (m, s, arithmetic) by the
 // autotuner below; all give identical results; a variant that does not
 // apply runs variant 0.
 struct MvVariant {

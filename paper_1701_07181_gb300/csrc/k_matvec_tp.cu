@@ -89,15 +89,16 @@ __device__ __forceinline__ void tp_consume2(df_acc2 (&acc)[S], const unsigned ch
         const float4 b0 = Jc[(c * B + a) >> 1], b1 = Jc[((c + 1) * B + a) >> 1];
         const f32x2 h0 = f2_pack(b0.x, b0.z), l0 = f2_pack(b0.y, b0.w);
         const f32x2 h1 = f2_pack(b1.x, b1.z), l1 = f2_pack(b1.y, b1.w);
+        const f32x2 n0 = f2_neg(h0), n1 = f2_neg(h1);  // once per column for all stages
 #pragma unroll
         for (int l = 0; l < S; ++l) {
             const float4 xv = *reinterpret_cast<const float4 *>(X + 2 * (l * B + c0 + c));
             if (XF) {
-                df_acc2_fma_f(acc[l], h0, l0, f2_pack(xv.x, xv.x), f2_pack(-xv.x, -xv.x));
-                df_acc2_fma_f(acc[l], h1, l1, f2_pack(xv.z, xv.z), f2_pack(-xv.z, -xv.z));
+                df_acc2_fma_f(acc[l], h0, n0, l0, f2_pack(xv.x, xv.x));
+                df_acc2_fma_f(acc[l], h1, n1, l1, f2_pack(xv.z, xv.z));
             } else {
-                df_acc2_fma(acc[l], h0, l0, f2_pack(xv.x, xv.x), f2_pack(-xv.x, -xv.x), f2_pack(xv.y, xv.y));
-                df_acc2_fma(acc[l], h1, l1, f2_pack(xv.z, xv.z), f2_pack(-xv.z, -xv.z), f2_pack(xv.w, xv.w));
+                df_acc2_fma(acc[l], h0, n0, l0, f2_pack(xv.x, xv.x), f2_pack(xv.y, xv.y));
+                df_acc2_fma(acc[l], h1, n1, l1, f2_pack(xv.z, xv.z), f2_pack(xv.w, xv.w));
             }
         }
         if (fold_after(c0 + c + 1, B))
@@ -302,11 +303,13 @@ bool run_matvec_tp(const MatvecParams &P, int *err, cudaStream_t st) {
     return true;
 }
 
-template <int S, int CK, int NU, int R = 1, int GO = 0>
+template <int S, int CK, int NU, int R = 1, int GO = 0, int MB = 0>
 bool run_matvec_tp_any(const MatvecParams &P, int *err, cudaStream_t st) {
-    return run_matvec_tp<S, 40, CK, NU, R, GO>(P, err, st) || run_matvec_tp<S, 50, CK, NU, R, GO>(P, err, st) ||
-           run_matvec_tp<S, 24, CK, NU, R, GO>(P, err, st) || run_matvec_tp<S, 20, CK, NU, R, GO>(P, err, st) ||
-           run_matvec_tp<S, 12, CK, NU, R, GO>(P, err, st);
+    return run_matvec_tp<S, 40, CK, NU, R, GO, 1, MB>(P, err, st) ||
+           run_matvec_tp<S, 50, CK, NU, R, GO, 1, MB>(P, err, st) ||
+           run_matvec_tp<S, 24, CK, NU, R, GO, 1, MB>(P, err, st) ||
+           run_matvec_tp<S, 20, CK, NU, R, GO, 1, MB>(P, err, st) ||
+           run_matvec_tp<S, 12, CK, NU, R, GO, 1, MB>(P, err, st);
 }
 
 template <int S>
@@ -317,7 +320,7 @@ bool run_tp_s(const MatvecParams &P, int form, int *err, cudaStream_t st) {
         case 7: return run_matvec_tp_any<S, 8, 3>(P, err, st);
         case 8: return run_matvec_tp_any<S, 8, 3, 2, 128>(P, err, st);
         case 9: return run_matvec_tp_any<S, 8, 2, 2, 128>(P, err, st);
-        case 10: return run_matvec_tp_any<S, 10, 2, 2, 128>(P, err, st);
+        case 10: return run_matvec_tp_any<S, 8, 2, 2, 128, 5>(P, err, st);
         default: return false;
     }
 }
