@@ -298,7 +298,9 @@ def precision_variants(dev):
     the oracle)."""
     import torch
     from paper_1701_07181_gb300 import inputs, irk
-    variants = (("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "df64"), ("bf16", "df64"))
+    # fp64-dfop: binary64 Krylov vectors, Gram-Schmidt and residual, the
+    # operator product alone in double-float
+    variants = (("fp64", "fp64"), ("fp32", "fp64"), ("fp32", "fp64-dfop"), ("fp32", "df64"), ("bf16", "df64"))
     gold = oracle_samples()
     out = {}
     for name, dts in (("c1", DTS), ("c2", (0.1,))):
@@ -307,7 +309,7 @@ def precision_variants(dev):
         rp, ci, J, M, R = t(P.row_ptr), t(P.col_idx), t(P.J), t(P.M), t(P.R)
         res, ref = {}, {}
         for fprec, kry in variants:
-            key = "%s_factors_%s_krylov" % (fprec, kry)
+            key = "%s_factors_%s_krylov" % (fprec, kry.replace("-", "_"))
             rows = {}
             with irk.Solver(P.s, P.T, P.m, rp, ci, J, M, precond="uncoupled", factor_prec=fprec, krylov=kry,
                             ordering="multicolor") as S:

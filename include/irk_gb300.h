@@ -94,8 +94,16 @@ enum irk_factor_precision { IRK_FACTOR_FP64 = 0, IRK_FACTOR_FP32 = 1, IRK_FACTOR
 /* Arithmetic of the outer Krylov method (operator product, Gram-Schmidt,
  * residuals).  FP64: IEEE binary64 on the FP64 pipe.  DF64: double-float
  * (pairs of binary32 with error-free transformations, about 48 significant
- * bits) on the FP32 pipe, which GB300 executes about 60x faster. */
-enum irk_krylov_arith { IRK_KRYLOV_FP64 = 0, IRK_KRYLOV_DF64 = 1 };
+ * bits) on the FP32 pipe, which GB300 executes about 60x faster.
+ * FP64_DFOP: binary64 Krylov vectors, Gram-Schmidt, Givens rotations and
+ * true residual, with the operator product alone in double-float: J and M
+ * are held as double-float pairs, each product's input is split into pairs
+ * before it and its result rounded back to binary64 after it (the residual
+ * form subtracts in binary64); the operator's accuracy is double-float's
+ * (about 1e-14 relative), the rest of the iteration binary64's.  J, M, dt and
+ * right-hand sides are treated as for DF64 (range checks and power-of-two
+ * scaling below).  Not accepted by irk_group_create. */
+enum irk_krylov_arith { IRK_KRYLOV_FP64 = 0, IRK_KRYLOV_DF64 = 1, IRK_KRYLOV_FP64_DFOP = 2 };
 
 enum irk_formulation { IRK_TRANSFORMED = 0, IRK_UNTRANSFORMED = 1 };
 
@@ -173,7 +181,8 @@ typedef struct {
 /* Fill *opt with the defaults listed above. */
 IRK_API void irk_default_options(irk_options *opt);
 
-/* Magnitude range of the double-float Krylov arithmetic (IRK_KRYLOV_DF64).
+/* Magnitude range of the double-float Krylov arithmetic (IRK_KRYLOV_DF64, and
+ * IRK_KRYLOV_FP64_DFOP, whose operator product is double-float).
  * A double-float value is a pair of binary32 numbers, so its exponent range
  * is binary32's: a magnitude above about 3.4e38 overflows, and below about
  * 1e-31 the low word turns subnormal and the value keeps fewer than 48

@@ -199,7 +199,7 @@ int load_values(irk_ctx *c, const double *J, const double *M, int mem_space) {
     memcpy(&mmx, &hmax[1], sizeof(double));
     c->jmax = jm;
     c->mmax = mmx;
-    if (c->df && (!df_range_ok(jm) || !df_range_ok(mmx))) return IRK_ERR_INVALID;
+    if (c->dfop && (!df_range_ok(jm) || !df_range_ok(mmx))) return IRK_ERR_INVALID;
     return IRK_OK;
 }
 
@@ -207,13 +207,13 @@ int load_values(irk_ctx *c, const double *J, const double *M, int mem_space) {
 // dt * max|J| within its range.
 bool dt_ok(const irk_ctx *c, double dt) {
     if (!std::isfinite(dt)) return false;
-    return !c->df || std::fabs(dt) * c->jmax <= IRK_DF64_MAX_MAGNITUDE;
+    return !c->dfop || std::fabs(dt) * c->jmax <= IRK_DF64_MAX_MAGNITUDE;
 }
 
-// Power-of-two scale of a double-float right-hand side in d_io (see the
-// header); null for binary64 (no scaling).
+// Power-of-two scale of a right-hand side in d_io when the operator product
+// is double-float (see the header); null for binary64 (no scaling).
 const double *rhs_scale(irk_ctx *c, int *rc) {
-    if (!c->df) return nullptr;
+    if (!c->dfop) return nullptr;
     *rc = launch_pow2_scale(c->stream, c->N, c->d_io, c->d_amax + 2, c->d_vscale);
     c->launches += 2;
     return c->d_vscale;
@@ -335,6 +335,8 @@ void free_ctx(irk_ctx *c) {
     cudaFree(c->d_V);
     cudaFree(c->d_Z);
     cudaFree(c->d_x);
+    cudaFree(c->d_xdf);
+    cudaFree(c->d_ydf);
     cudaFree(c->d_b);
     cudaFree(c->d_io);
     cudaFree(c->d_H);
@@ -413,7 +415,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
     int rc = IRK_OK;
     if (c->opt.restart < 1 || c->opt.restart > IRK_MAX_RESTART || c->opt.max_iter < 0 ||
         c->opt.precond < IRK_PC_NONE || c->opt.precond > IRK_PC_ELEMENT || c->opt.factor_prec < 0 ||
-        c->opt.factor_prec > IRK_FACTOR_BF16 || c->opt.krylov_arith < 0 || c->opt.krylov_arith > 1 ||
+        c->opt.factor_prec > IRK_FACTOR_BF16 || c->opt.krylov_arith < 0 || c->opt.krylov_arith > IRK_KRYLOV_FP64_DFOP ||
         c->opt.formulation < 0 || c->opt.formulation > 1 || c->opt.sweep < 0 || c->opt.sweep > 1 ||
         c->opt.ordering < 0 || c->opt.ordering > 1 || c->opt.partitions < 0 || c->opt.stage_jacobians < 0 ||
         c->opt.stage_jacobians > 1 || c->opt.spin_limit < 0 || c->opt.orthogonalization < 0 ||
@@ -427,6 +429,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
     c->T = T;
     c->m = m;
     c->df = c->opt.krylov_arith == IRK_KRYLOV_DF64;
+    c->dfop = c->opt.krylov_arith == IRK_KRYLOV_DF64 || c->opt.krylov_arith == IRK_KRYLOV_FP64_DFOP;
     c->fprec = c->opt.factor_prec;
     c->nJ = (c->opt.stage_jacobians && s > 1) ? s : 1;
     c->spin = c->opt.spin_limit > 0 ? c->opt.spin_limit : IRK_DEFAULT_SPIN_LIMIT;
@@ -508,6 +511,8 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
               cudaMalloc(&c->d_V, sizeof(vec8) * (size_t)c->N * (R + 1)) == cudaSuccess &&
               cudaMalloc(&c->d_Z, sizeof(vec8) * (size_t)c->N * R) == cudaSuccess &&
               cudaMalloc(&c->d_x, sizeof(vec8) * (size_t)c->N) == cudaSuccess &&
+              (c->df || !c->dfop || (cudaMalloc(&c->d_xdf, sizeof(vec8) * (size_t)c->N) == cudaSuccess &&
+                                     cudaMalloc(&c->d_ydf, sizeof(vec8) * (size_t)c->N) == cudaSuccess)) &&
               cudaMalloc(&c->d_b, sizeof(vec8) * (size_t)c->N) == cudaSuccess &&
               cudaMalloc(&c->d_io, sizeof(double) * (size_t)c->N) == cudaSuccess &&
               cudaMalloc(&c->d_H, sizeof(double) * (R + 1) * R) == cudaSuccess &&
@@ -687,7 +692,7 @@ int irk_solve(irk_ctx *c, const double *Rhs, double dt, double rtol, double *W, 
     bool x_zero = true;
     // binary32 factors write binary32-valued z_j = P^{-1} v_j (double-float
     // with zero low words): their operator products skip those words
-    const int z_f32 = c->df && c->pc.kind != IRK_PC_NONE && c->fprec != IRK_FACTOR_FP64;
+    const int z_f32 = c->dfop && c->pc.kind != IRK_PC_NONE && c->fprec != IRK_FACTOR_FP64;
     while (rc == IRK_OK && bnorm > 0.0) {
         vec8 *V0 = c->d_V;
         if (x_zero) {

@@ -91,7 +91,8 @@ struct irk_ctx {
     long long n = 0, N = 0;  // n = T m, N = s n
     double A[IRK_MAX_S * IRK_MAX_S], Ainv[IRK_MAX_S * IRK_MAX_S], shift[IRK_MAX_S];
     irk_options opt;
-    int df = 0;  // 1: Krylov arithmetic is double-float
+    int df = 0;    // 1: Krylov vectors and arithmetic are double-float
+    int dfop = 0;  // 1: J, M and the operator product are double-float (DF64, FP64_DFOP)
     int fprec = IRK_FACTOR_FP64;
     std::vector<int> h_rp, h_ci;
     std::vector<int> h_part;  // optional partition id per element (Sec. 4.5)
@@ -103,6 +104,7 @@ struct irk_ctx {
     double factored_dt = 0.0;
     // Krylov workspace
     vec8 *d_V = nullptr, *d_Z = nullptr, *d_x = nullptr, *d_b = nullptr, *d_r = nullptr;
+    vec8 *d_xdf = nullptr, *d_ydf = nullptr;  // FP64_DFOP: the operator's input and output as pairs
     double *d_io = nullptr;  // stage-major binary64 staging for inputs / outputs (2 N)
     double *d_H = nullptr;   // (restart+1) x restart Hessenberg, binary64
     double *d_cs = nullptr, *d_sn = nullptr, *d_g = nullptr, *d_yls = nullptr;

@@ -2234,7 +2234,7 @@ static int factor_impl(irk_ctx *c, double dt) {
         for (int q = 0; q < s * s; ++q) tab.cm[q] = C0[q];
         k_assemble_elem<C><<<grid_cap(P.nnz * P.b * P.b), 256, 0, c->stream>>>(
             P.nnz, s, c->m, transformed ? 0 : 1, P.d_rowof, P.d_ci, c->d_J,
-            c->nJ > 1 ? (long long)c->nnzb * c->m * c->m : 0LL, c->d_M, c->df, tab, dt, (C *)P.d_vals);
+            c->nJ > 1 ? (long long)c->nnzb * c->m * c->m : 0LL, c->d_M, c->dfop, tab, dt, (C *)P.d_vals);
     } else {
         if (P.kind == IRK_PC_UNCOUPLED) {
             for (int k = 0; k < s; ++k) tab.cm[k * s + k] = c->Ainv[k * s + k] + c->shift[k];
@@ -2248,10 +2248,10 @@ static int factor_impl(irk_ctx *c, double dt) {
         }
         if (P.kind == IRK_PC_UNCOUPLED && c->nJ == 1 && P.nnz % s == 0)
             k_assemble_stages<C><<<grid_cap(P.nnz / s * 256), 256, 0, c->stream>>>(
-                P.nnz / s, s, c->m, P.d_asm, c->d_J, c->d_M, c->df, tab, (C *)P.d_vals);
+                P.nnz / s, s, c->m, P.d_asm, c->d_J, c->d_M, c->dfop, tab, (C *)P.d_vals);
         else
             k_assemble<C><<<grid_cap(P.nnz * 256), 256, 0, c->stream>>>(P.nnz, c->m, P.d_asm, c->d_J, c->d_M,
-                                                                       c->df, tab, (C *)P.d_vals);
+                                                                       c->dfop, tab, (C *)P.d_vals);
     }
     c->launches++;
     tmark_end(c, tm, 3);

@@ -824,7 +824,7 @@ std::map<long long, int> g_tune;
 int tune_key_variant(irk_ctx *c, const MatvecParams &P) {
     // irk_kernel_options.matvec_variant pins the variant (tests compare them)
     if (c->ko.matvec_variant >= 0 && c->ko.matvec_variant < kNumMvVariants) return c->ko.matvec_variant;
-    const long long key = ((long long)c->m << 20) | ((long long)c->s << 4) | c->df;
+    const long long key = ((long long)c->m << 20) | ((long long)c->s << 4) | c->dfop;
     {
         std::lock_guard<std::mutex> g(g_tune_mu);
         auto it = g_tune.find(key);
@@ -840,7 +840,7 @@ int tune_key_variant(irk_ctx *c, const MatvecParams &P) {
         float t[5];
         for (int rep = 0; rep < 6; ++rep) {
             cudaEventRecord(e0, c->stream);
-            if (c->df)
+            if (c->dfop)
                 dispatch_s<ArDF>(c->s, P, v, c->d_err, c->stream);
             else
                 dispatch_s<ArF64>(c->s, P, v, c->d_err, c->stream);
@@ -891,7 +891,7 @@ int launch_matvec_ps(irk_ctx *c, MatvecParams P) {
         }
         P.form = IRK_TRANSFORMED;
     }
-    if (c->df)
+    if (c->dfop)
         dispatch_ps<ArDF>(c->s, P, untransformed, c->stream);
     else
         dispatch_ps<ArF64>(c->s, P, untransformed, c->stream);
@@ -906,6 +906,22 @@ int irk_matvec_variants() { return kNumMvVariants; }
 // chosen variant of a context's class (-1 before the first product)
 int matvec_variant(const irk_ctx *c) { return c->mv_variant; }
 
+// binary64 vector -> double-float pairs (IRK_KRYLOV_FP64_DFOP operator input)
+__global__ void k_split_df(long long n, const vec8 *x, vec8 *xd) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        ArDF::st(xd + i, ArDF::from_double(ArF64::ld(x + i)));
+}
+
+// double-float pairs -> binary64 (hi + lo rounded once), or in the residual
+// form rhs - (hi + lo) in binary64
+__global__ void k_join_df(long long n, const vec8 *yd, const vec8 *rhs, vec8 *y) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double v = ArDF::to_double(ArDF::ld(yd + i));
+        ArF64::st(y + i, rhs ? ArF64::ld(rhs + i) - v : v);
+    }
+}
+
 int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt, int mode, int x_f32) {
     MatvecParams P;
     memset(&P, 0, sizeof(P));
@@ -913,7 +929,7 @@ int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt
     P.m = c->m;
     P.form = c->opt.formulation;
     P.mode = mode;
-    P.xf32 = (x_f32 && c->df) ? 1 : 0;
+    P.xf32 = (x_f32 && c->dfop) ? 1 : 0;
     P.rp = c->d_rp;
     P.ci = c->d_ci;
     P.J = c->d_J;
@@ -924,14 +940,36 @@ int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt
     const double *C = (P.form == IRK_TRANSFORMED) ? c->Ainv : c->A;
     for (int q = 0; q < c->s * c->s; ++q) P.C[q] = make_kcoef(C[q]);
     P.mdt = make_kcoef(-dt);
-    if (c->nJ > 1) return launch_matvec_ps(c, P);
-    if (c->mv_variant < 0) c->mv_variant = tune_key_variant(c, P);
-    if (c->df)
-        dispatch_s<ArDF>(c->s, P, c->mv_variant, c->d_err, c->stream);
-    else
-        dispatch_s<ArF64>(c->s, P, c->mv_variant, c->d_err, c->stream);
-    c->launches++;
-    return cuda_status(cudaGetLastError());
+    // binary64 vectors with the double-float product: split the input into
+    // pairs, multiply into pairs, round back (and subtract) in binary64
+    const bool split = c->dfop && !c->df;
+    const int g = grid_for(c->N, 256);
+    if (split) {
+        k_split_df<<<g, 256, 0, c->stream>>>(c->N, x, c->d_xdf);
+        c->launches++;
+        P.x = c->d_xdf;
+        P.y = c->d_ydf;
+        P.mode = 0;
+        P.rhs = nullptr;
+    }
+    int rc;
+    if (c->nJ > 1) {
+        rc = launch_matvec_ps(c, P);
+    } else {
+        if (c->mv_variant < 0) c->mv_variant = tune_key_variant(c, P);
+        if (c->dfop)
+            dispatch_s<ArDF>(c->s, P, c->mv_variant, c->d_err, c->stream);
+        else
+            dispatch_s<ArF64>(c->s, P, c->mv_variant, c->d_err, c->stream);
+        c->launches++;
+        rc = cuda_status(cudaGetLastError());
+    }
+    if (split && !rc) {
+        k_join_df<<<g, 256, 0, c->stream>>>(c->N, c->d_ydf, mode == 1 ? rhs : nullptr, y);
+        c->launches++;
+        rc = cuda_status(cudaGetLastError());
+    }
+    return rc;
 }
 
 // y = (I_s (x) J) x: the Jacobian product alone (right-hand sides of DIRK
@@ -951,11 +989,23 @@ int launch_jacobian(irk_ctx *c, const vec8 *x, vec8 *y) {
     P.rhs = nullptr;
     P.y = y;
     P.mdt = make_kcoef(0.0);
-    if (c->df)
+    const bool split = c->dfop && !c->df;
+    const int g = grid_for(c->N, 256);
+    if (split) {
+        k_split_df<<<g, 256, 0, c->stream>>>(c->N, x, c->d_xdf);
+        c->launches++;
+        P.x = c->d_xdf;
+        P.y = c->d_ydf;
+    }
+    if (c->dfop)
         dispatch_s<ArDF>(c->s, P, 0, c->d_err, c->stream);
     else
         dispatch_s<ArF64>(c->s, P, 0, c->d_err, c->stream);
     c->launches++;
+    if (split) {
+        k_join_df<<<g, 256, 0, c->stream>>>(c->N, c->d_ydf, nullptr, y);
+        c->launches++;
+    }
     return cuda_status(cudaGetLastError());
 }
 
@@ -998,7 +1048,7 @@ int launch_convert_blocks(irk_ctx *c, const double *src, vec8 *dst, long long nb
                           int *err) {
     long long total = nblocks * c->m * c->m;
     int g = grid_for(total, 256);
-    if (c->df)
+    if (c->dfop)
         k_convert_blocks<ArDF><<<g, 256, 0, c->stream>>>(total, c->m, src, dst, amax, err);
     else
         k_convert_blocks<ArF64><<<g, 256, 0, c->stream>>>(total, c->m, src, dst, amax, err);

@@ -21,7 +21,7 @@ IRK_OK, IRK_NOT_CONVERGED = 0, 1
 IRK_HOST, IRK_DEVICE = 0, 1
 PRECOND = {"none": 0, "uncoupled": 1, "coupled": 2, "element": 3}
 FACTOR_PREC = {"fp64": 0, "fp32": 1, "bf16": 2}
-KRYLOV = {"fp64": 0, "df64": 1}
+KRYLOV = {"fp64": 0, "df64": 1, "fp64-dfop": 2}
 FORM = {"transformed": 0, "untransformed": 1}
 
 _lock = threading.Lock()

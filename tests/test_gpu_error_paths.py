@@ -135,8 +135,9 @@ def test_spin_limit_rejects_negative():
         assert e.value.code == INVALID
 
 
+@pytest.mark.parametrize("krylov", ["df64", "fp64-dfop"])
 @pytest.mark.parametrize("scale", [1e-35, 1e39])
-def test_df64_rhs_out_of_binary32_range(scale):
+def test_df64_rhs_out_of_binary32_range(scale, krylov):
     """R scaled far outside binary32's range: W within the 1e-6 bar of the
     oracle's solution for the scaled R (binary64 throughout)."""
     irk = _irk()
@@ -144,7 +145,7 @@ def test_df64_rhs_out_of_binary32_range(scale):
     R = P.R * scale
     W_ref = ref_solution(P, R=R)
     with irk.Solver(P.s, P.T, P.m, dev(P.row_ptr), dev(P.col_idx), dev(P.J), dev(P.M), precond="uncoupled",
-                    factor_prec="fp32", krylov="df64") as S:
+                    factor_prec="fp32", krylov=krylov) as S:
         W, it, rr, rc = S.solve(dev(R), 0.1, rtol=1e-8)
         y = S.apply_operator(dev(R), 0.1)
     assert rc == 0 and rr <= 1e-8
@@ -165,21 +166,34 @@ def test_df64_power_of_two_scaling_is_exact():
     assert torch.equal(torch.ldexp(W2, torch.tensor(90.0, dtype=torch.float64, device=W2.device)), W1)
 
 
-def test_df64_refuses_out_of_range_values_and_dt():
+@pytest.mark.parametrize("krylov", ["df64", "fp64-dfop"])
+def test_df64_refuses_out_of_range_values_and_dt(krylov):
     irk = _irk()
     P = problem()
     with pytest.raises(irk.IrkError) as e:
-        irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J * 1e35, P.M, krylov="df64", factor_prec="fp32")
+        irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J * 1e35, P.M, krylov=krylov, factor_prec="fp32")
     assert e.value.code == INVALID
     with pytest.raises(irk.IrkError) as e:
-        irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M * 1e-35, krylov="df64", factor_prec="fp32")
+        irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M * 1e-35, krylov=krylov, factor_prec="fp32")
     assert e.value.code == INVALID
     # binary64 Krylov arithmetic has binary64's range
     with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J * 1e35, P.M, krylov="fp64") as S:
         S.factor(1e-35)
-    with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, krylov="df64", factor_prec="fp32") as S:
+    with irk.Solver(P.s, P.T, P.m, P.row_ptr, P.col_idx, P.J, P.M, krylov=krylov, factor_prec="fp32") as S:
         with pytest.raises(irk.IrkError) as e:
             S.solve(P.R, 1e31, rtol=1e-8)
         assert e.value.code == INVALID
         W, it, rr, rc = S.solve(P.R, 0.1, rtol=1e-8)  # the context is unaffected
         assert rc == 0 and rr <= 1e-8
+
+
+def test_group_refuses_split_precision():
+    """The multi-request engine runs binary64 or double-float Krylov only."""
+    irk = _irk()
+    import ctypes
+    lib = irk.load()
+    opt = irk.Options()
+    lib.irk_default_options(ctypes.byref(opt))
+    opt.krylov_arith = irk.KRYLOV["fp64-dfop"]
+    h = ctypes.c_void_p()
+    assert lib.irk_group_create(ctypes.byref(h), 2, None, 12, 1000, 4000, 4, ctypes.byref(opt)) == -1

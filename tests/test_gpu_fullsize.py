@@ -30,7 +30,7 @@ from _parity import rel
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
-VARIANTS = [("fp32", "df64"), ("fp32", "fp64"), ("bf16", "df64"), ("fp64", "fp64")]
+VARIANTS = [("fp32", "df64"), ("fp32", "fp64"), ("fp32", "fp64-dfop"), ("bf16", "df64"), ("fp64", "fp64")]
 
 
 def _irk():

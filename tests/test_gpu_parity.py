@@ -56,7 +56,7 @@ def solver(P, host=False, **kw):
     return irk.Solver(P.s, P.T, P.m, dev(P.row_ptr), dev(P.col_idx), dev(P.J), dev(P.M), **kw)
 
 
-@pytest.mark.parametrize("krylov", ["fp64", "df64"])
+@pytest.mark.parametrize("krylov", ["fp64", "df64", "fp64-dfop"])
 @pytest.mark.parametrize("form", ["transformed", "untransformed"])
 @pytest.mark.parametrize("kind,s,m", [("2d", 2, 12), ("3d", 3, 20), ("chain", 1, 7), ("chain", 5, 3),
                                       ("2d", 3, 40), ("c0", 2, 12), ("2d", 4, 1)])
@@ -147,7 +147,27 @@ def test_mixed_solve_within_1e6_of_oracle(fprec, kind, s, m):
     assert rel(W, W_ref) <= 1e-6
 
 
-@pytest.mark.parametrize("krylov", ["fp64", "df64"])
+@pytest.mark.parametrize("fprec", ["fp32", "bf16"])
+@pytest.mark.parametrize("kind,s,m", [("2d", 3, 40), ("3d", 3, 20), ("c0", 2, 12)])
+def test_split_precision_solve(fprec, kind, s, m):
+    """Binary64 Krylov vectors, Gram-Schmidt and residual with the operator
+    product alone in double-float (krylov="fp64-dfop"): W within 1e-6 of
+    the FP64 oracle at rtol 1e-8, and the iteration count of the binary64
+    path with the same factors within one."""
+    P = problem(kind, s, m)
+    ref = ref_of(P)
+    W_ref = ref.solve(P.R, P.dt, rtol=1e-12)["x"]
+    its = []
+    for kry in ("fp64-dfop", "fp64"):
+        with solver(P, precond="uncoupled", factor_prec=fprec, krylov=kry) as S:
+            W, iters, relres, rc = S.solve(dev(P.R), P.dt, rtol=1e-8)
+        assert rc == 0 and relres <= 1e-8
+        assert rel(W, W_ref) <= 1e-6
+        its.append(iters)
+    assert abs(its[0] - its[1]) <= 1, its
+
+
+@pytest.mark.parametrize("krylov", ["fp64", "df64", "fp64-dfop"])
 @pytest.mark.parametrize("s,expect", [(1, 0.5), (2, 4.0 / 11.0), (3, 39.0 / 106.0)])
 def test_scalar_problem_pade_on_gpu(krylov, s, expect):
     """u' = lambda u with dt*lambda = -1: u1 = u0 + dt w_s = R(-1) u0 (Sec. 4.1)."""
