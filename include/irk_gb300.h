@@ -444,7 +444,9 @@ typedef struct {
      * with two rows per consumer thread in packed two-lane binary32
      * arithmetic and about 128 consumer threads per CTA ((8, 3) and (8, 2)
      * chunk columns and units, and (8, 2) with registers capped for five
-     * CTAs per SM); -1 before the first product.  irk_kernel_options.matvec_variant pins the variant.  Every variant
+     * CTAs per SM), 17 and 18 the (8, 2) two-row kernel taking element rows
+     * from a run-time counter (five and four CTAs per SM); -1 before the
+     * first product.  irk_kernel_options.matvec_variant pins the variant.  Every variant
      * gives the same result bit for bit. */
     int matvec_variant;
     /* with irk_options.timing = 1: device time of the kernels of the last
@@ -475,7 +477,7 @@ IRK_API int irk_get_stats(const irk_ctx *ctx, irk_stats *out);
  * gives the same result bit for bit except where noted. */
 typedef struct {
     int matvec_variant;     /* -1 (default): operator-product launch variant
-                               autotuned per (m, s, arithmetic); 0..16 pin one
+                               autotuned per (m, s, arithmetic); 0..18 pin one
                                (see irk_stats.matvec_variant) */
     int sweep_two_colour;   /* 1 (default): the two-launch preconditioner
                                application where the element order allows it

@@ -335,6 +335,7 @@ void free_ctx(irk_ctx *c) {
     cudaFree(c->d_V);
     cudaFree(c->d_Z);
     cudaFree(c->d_x);
+    cudaFree(c->d_rowctr);
     cudaFree(c->d_xdf);
     cudaFree(c->d_ydf);
     cudaFree(c->d_b);
@@ -511,6 +512,7 @@ int irk_setup(irk_ctx **out, int s, const double *A, int T, int m, const int32_t
               cudaMalloc(&c->d_V, sizeof(vec8) * (size_t)c->N * (R + 1)) == cudaSuccess &&
               cudaMalloc(&c->d_Z, sizeof(vec8) * (size_t)c->N * R) == cudaSuccess &&
               cudaMalloc(&c->d_x, sizeof(vec8) * (size_t)c->N) == cudaSuccess &&
+              cudaMalloc(&c->d_rowctr, sizeof(int)) == cudaSuccess &&
               (c->df || !c->dfop || (cudaMalloc(&c->d_xdf, sizeof(vec8) * (size_t)c->N) == cudaSuccess &&
                                      cudaMalloc(&c->d_ydf, sizeof(vec8) * (size_t)c->N) == cudaSuccess)) &&
               cudaMalloc(&c->d_b, sizeof(vec8) * (size_t)c->N) == cudaSuccess &&

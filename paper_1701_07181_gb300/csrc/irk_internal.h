@@ -105,6 +105,7 @@ struct irk_ctx {
     // Krylov workspace
     vec8 *d_V = nullptr, *d_Z = nullptr, *d_x = nullptr, *d_b = nullptr, *d_r = nullptr;
     vec8 *d_xdf = nullptr, *d_ydf = nullptr;  // FP64_DFOP: the operator's input and output as pairs
+    int *d_rowctr = nullptr;  // row counter of the dynamically scheduled operator kernel
     double *d_io = nullptr;  // stage-major binary64 staging for inputs / outputs (2 N)
     double *d_H = nullptr;   // (restart+1) x restart Hessenberg, binary64
     double *d_cs = nullptr, *d_sn = nullptr, *d_g = nullptr, *d_yls = nullptr;

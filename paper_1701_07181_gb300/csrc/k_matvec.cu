@@ -671,21 +671,24 @@ int grid_for(long long work, int threads) {
 // with (columns per unit, units in the ring) = (8, 4), (16, 2), (8, 3).
 // 14-16: k_matvec_tp with two rows per consumer thread in packed two-lane
 // arithmetic and about 128 consumer threads per CTA, (8, 3), (8, 2), and
-// (8, 2) with registers capped for five CTAs per SM.  Picked per (m, s, arithmetic) by the
+// (8, 2) with registers capped for five CTAs per SM.  17-18: the (8, 2)
+// two-row kernel with element rows handed out at run time from a counter
+// (k_matvec_tpd), five and four CTAs per SM.  Picked per (m, s, arithmetic) by the
 // autotuner below; all give identical results; a variant that does not
 // apply runs variant 0.
 struct MvVariant {
     int ch, threads;  // k_matvec / k_matvec_b
     int ns, per_sm;   // k_matvec_pipe (ns > 0)
     int fixed;        // 1: k_matvec_b, 2: k_matvec_rb, 3: k_matvec_b with CH = 8, 4: k_matvec_sp,
-                      // 5-7: k_matvec_tp, 8-10: k_matvec_tp with two rows per thread
+                      // 5-7: k_matvec_tp, 8-10: k_matvec_tp with two rows per thread,
+                      // 11-12: k_matvec_tpd
 };
 const MvVariant kMvVariants[] = {{8, 256, 0, 0, 0}, {4, 256, 0, 0, 0}, {2, 256, 0, 0, 0}, {4, 128, 0, 0, 0},
                                  {0, 0, 2, 1, 0},   {0, 0, 3, 1, 0},   {0, 0, 2, 2, 0},   {4, 256, 0, 0, 1},
                                  {2, 256, 0, 0, 2}, {8, 256, 0, 0, 3}, {4, 256, 0, 0, 4}, {0, 0, 0, 0, 5},
                                  {0, 0, 0, 0, 6},   {0, 0, 0, 0, 7},   {0, 0, 0, 0, 8},   {0, 0, 0, 0, 9},
-                                 {0, 0, 0, 0, 10}};
-const int kNumMvVariants = 17;
+                                 {0, 0, 0, 0, 10},  {0, 0, 0, 0, 11},  {0, 0, 0, 0, 12}};
+const int kNumMvVariants = 19;
 
 // Groups per CTA of a pipelined variant (0: not applicable).  Needs m even
 // (16-byte multiples for the bulk copies) and 16-byte aligned operands.
@@ -937,6 +940,7 @@ int launch_matvec(irk_ctx *c, const vec8 *x, vec8 *y, const vec8 *rhs, double dt
     P.x = x;
     P.rhs = rhs;
     P.y = y;
+    P.rowctr = c->d_rowctr;
     const double *C = (P.form == IRK_TRANSFORMED) ? c->Ainv : c->A;
     for (int q = 0; q < c->s * c->s; ++q) P.C[q] = make_kcoef(C[q]);
     P.mdt = make_kcoef(-dt);

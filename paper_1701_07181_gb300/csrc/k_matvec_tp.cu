@@ -282,6 +282,194 @@ __global__ void __launch_bounds__(TpShape<S, B, CK, NU, R, GO, PW>::THREADS,
     }
 }
 
+// k_matvec_tp with the element rows handed out at run time: each producer
+// lane takes its group's next row from a global counter (one row ahead of
+// the one it streams), so that every group keeps working until the rows run
+// out instead of a fixed share of rows leaving a tail of groups with one row
+// more than the others.  The producer writes each row's index and block
+// count into a two-entry table of its group before the row's first unit; the
+// consumers read it after that unit's "full" barrier (whose completion orders
+// the write before their read), and a row index of -1, published with a
+// "full" arrival that carries no copy, ends the group.  The table entry of a
+// row is rewritten two rows later, by which time its consumers have moved on
+// (a row spans more units than the ring holds).  Same accumulation order as
+// every other variant.
+template <int S, int B, bool XF, int CK, int NU, int R, int GO, int MB>
+__global__ void __launch_bounds__(TpShape<S, B, CK, NU, R, GO, 1>::THREADS, MB)
+    k_matvec_tpd(MatvecParams P, int *err) {
+    using SH = TpShape<S, B, CK, NU, R, GO, 1>;
+    using ACC = typename std::conditional<R == 1, df_acc, df_acc2>::type;
+    constexpr int G = SH::G;
+    constexpr long long BB = (long long)B * B, SB = (long long)S * B;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned long long *full = reinterpret_cast<unsigned long long *>(smem_raw);  // [G][NU]
+    unsigned long long *empty = full + G * NU;                                   // [G][NU]
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(smem_raw + 2 * NU * G * 8);
+    __shared__ int2 s_row[G][2];  // (row, J blocks) of a group's rows, by row ordinal parity
+    unsigned char *ring = smem_raw + SH::HEADER;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int q = 0; q < G * NU; ++q) {
+            mbar_init_n(full + q, 1);
+            mbar_init_n(empty + q, SH::BT);
+        }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid >= SH::CONS) {
+        const int g = tid - SH::CONS;
+        if (g >= G) return;
+        unsigned long long *fb = full + g * NU, *eb = empty + g * NU;
+        unsigned char *gr = ring + g * SH::GROUP;
+        int issued = 0, nblk = 0, nrow = 0, qend = -1;
+        bool ok = true;
+        int i = atomicAdd(P.rowctr, 1);
+        int p0 = 0, p1 = 0;
+        if (i < P.T) {
+            p0 = P.rp[i];
+            p1 = P.rp[i + 1];
+        }
+        while (ok) {
+            // the slot of the row's first unit (or of the end marker)
+            const int q0 = issued % NU;
+            if (issued >= NU && !mbar_wait(eb + q0, (unsigned)((issued / NU) - 1) & 1u)) {
+                atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+                *abort_flag = 1;
+                break;
+            }
+            if (i >= P.T) {  // no rows left: end marker, a "full" arrival without a copy
+                s_row[g][nrow & 1] = make_int2(-1, 0);
+                mbar_arrive(fb + q0);
+                qend = q0;
+                break;
+            }
+            s_row[g][nrow & 1] = make_int2(i, p1 - p0);
+            const int in = atomicAdd(P.rowctr, 1);  // the next row, consumed after this one
+            const int pend = P.form != IRK_FORM_JACOBIAN ? p1 : p1 - 1;  // p == p1: the mass block
+            int cnext = p0 < p1 ? P.ci[p0] : i;
+            for (int p = p0; p <= pend && ok; ++p, ++nblk) {
+                const int col = cnext;
+                if (p + 1 < p1) cnext = P.ci[p + 1];
+                const vec8 *blk = p < p1 ? P.J + (long long)p * BB : P.M + (long long)i * BB;
+                const vec8 *xs = P.x + (long long)(p < p1 ? col : i) * SB;
+                for (int c0 = 0; c0 < B; c0 += CK) {
+                    const int nc = B - c0 < CK ? B - c0 : CK;
+                    const int q = issued % NU;
+                    // the first unit's slot was waited for above
+                    if (!(p == p0 && c0 == 0) && issued >= NU &&
+                        !mbar_wait(eb + q, (unsigned)((issued / NU) - 1) & 1u)) {
+                        atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+                        *abort_flag = 1;
+                        ok = false;
+                        break;
+                    }
+                    if (*abort_flag) {
+                        ok = false;
+                        break;
+                    }
+                    const unsigned jb = (unsigned)(nc * B * 8);
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    if (c0 == 0) {
+                        mbar_expect_arrive(fb + q, jb + (unsigned)SH::XSLOT);
+                        tma_load_1d(gr + NU * SH::UNIT + (nblk % SH::NX) * SH::XSLOT, xs, (unsigned)SH::XSLOT, fb + q);
+                    } else {
+                        mbar_expect_arrive(fb + q, jb);
+                    }
+                    tma_load_1d(gr + q * SH::UNIT, blk + (long long)c0 * B, jb, fb + q);
+                    ++issued;
+                }
+            }
+            ++nrow;
+            i = in;
+            if (i < P.T) {
+                p0 = P.rp[i];
+                p1 = P.rp[i + 1];
+            }
+        }
+        // no copy into this CTA's shared memory may be in flight when it
+        // exits; the end marker completed one more phase of its slot, whose
+        // earlier copy had landed before the marker was sent
+        for (int u = issued > NU ? issued - NU : 0; u < issued; ++u)
+            mbar_wait(fb + u % NU, ((unsigned)(u / NU) + (u % NU == qend ? 1u : 0u)) & 1u);
+        return;
+    }
+    const int g = tid / SH::BT, a = (tid - g * SH::BT) * R;
+    if (g >= G) return;
+    unsigned long long *fb = full + g * NU, *eb = empty + g * NU;
+    const unsigned char *gr = ring + g * SH::GROUP;
+    int used = 0, nblk = 0;
+    for (int nrow = 0;; ++nrow) {
+        const int q0 = used % NU;
+        if (!mbar_wait(fb + q0, (unsigned)(used / NU) & 1u)) {
+            atomicOr(err, IRK_DEV_ERR_TIMEOUT);
+            *abort_flag = 1;
+            return;
+        }
+        const int2 row = s_row[g][nrow & 1];
+        if (row.x < 0) return;
+        const int i = row.x, nb = row.y;
+        ACC t[S], z[S];
+#pragma unroll
+        for (int l = 0; l < S; ++l) {
+            if constexpr (R == 1) {
+                t[l] = df_acc_zero();
+                z[l] = df_acc_zero();
+            } else {
+                t[l] = df_acc2_zero();
+                z[l] = df_acc2_zero();
+            }
+        }
+        for (int p = 0; p < nb; ++p)
+            if (!tp_block<S, B, XF, CK, NU, R, GO, 1>(t, gr, fb, eb, used, nblk++, a, err, abort_flag)) return;
+        if (P.form != IRK_FORM_JACOBIAN &&
+            !tp_block<S, B, XF, CK, NU, R, GO, 1>(z, gr, fb, eb, used, nblk++, a, err, abort_flag))
+            return;
+        if constexpr (R == 1) {
+            store_row<ArDF, S>(P, i, a, t, z);
+        } else {
+            df_acc t0[S], t1[S], z0[S], z1[S];
+#pragma unroll
+            for (int l = 0; l < S; ++l) {
+                df_acc2_split(t[l], t0[l], t1[l]);
+                df_acc2_split(z[l], z0[l], z1[l]);
+            }
+            store_row<ArDF, S>(P, i, a, t0, z0);
+            store_row<ArDF, S>(P, i, a + 1, t1, z1);
+        }
+    }
+}
+
+template <int S, int B, int CK, int NU, int R, int GO, int MB>
+bool run_matvec_tpd(const MatvecParams &P, int *err, cudaStream_t st) {
+    if (P.m != B || !P.rowctr || P.form == IRK_FORM_JACOBIAN) return false;
+    using SH = TpShape<S, B, CK, NU, R, GO, 1>;
+    const void *kern = P.xf32 ? (const void *)k_matvec_tpd<S, B, true, CK, NU, R, GO, MB>
+                              : (const void *)k_matvec_tpd<S, B, false, CK, NU, R, GO, MB>;
+    if (irk_allow_max_smem(kern)) return false;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, SH::THREADS, SH::SMEM) != cudaSuccess ||
+        per_sm <= 0)
+        return false;
+    const long long need = (P.T + SH::G - 1) / SH::G;
+    const long long grid = std::max(1LL, std::min<long long>(need, (long long)dev_limits().sms * per_sm));
+    if (cudaMemsetAsync(P.rowctr, 0, sizeof(int), st) != cudaSuccess) return false;
+    if (P.xf32)
+        k_matvec_tpd<S, B, true, CK, NU, R, GO, MB><<<(int)grid, SH::THREADS, SH::SMEM, st>>>(P, err);
+    else
+        k_matvec_tpd<S, B, false, CK, NU, R, GO, MB><<<(int)grid, SH::THREADS, SH::SMEM, st>>>(P, err);
+    return true;
+}
+
+template <int S, int CK, int NU, int R, int GO, int MB>
+bool run_matvec_tpd_any(const MatvecParams &P, int *err, cudaStream_t st) {
+    return run_matvec_tpd<S, 40, CK, NU, R, GO, MB>(P, err, st) ||
+           run_matvec_tpd<S, 50, CK, NU, R, GO, MB>(P, err, st) ||
+           run_matvec_tpd<S, 24, CK, NU, R, GO, MB>(P, err, st) ||
+           run_matvec_tpd<S, 20, CK, NU, R, GO, MB>(P, err, st) ||
+           run_matvec_tpd<S, 12, CK, NU, R, GO, MB>(P, err, st);
+}
+
 template <int S, int B, int CK, int NU, int R, int GO = 0, int PW = 1, int MB = 0>
 bool run_matvec_tp(const MatvecParams &P, int *err, cudaStream_t st) {
     if (P.m != B) return false;
@@ -321,6 +509,8 @@ bool run_tp_s(const MatvecParams &P, int form, int *err, cudaStream_t st) {
         case 8: return run_matvec_tp_any<S, 8, 3, 2, 128>(P, err, st);
         case 9: return run_matvec_tp_any<S, 8, 2, 2, 128>(P, err, st);
         case 10: return run_matvec_tp_any<S, 8, 2, 2, 128, 5>(P, err, st);
+        case 11: return run_matvec_tpd_any<S, 8, 2, 2, 128, 5>(P, err, st);
+        case 12: return run_matvec_tpd_any<S, 8, 2, 2, 128, 4>(P, err, st);
         default: return false;
     }
 }

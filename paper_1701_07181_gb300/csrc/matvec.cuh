@@ -23,6 +23,9 @@ struct MatvecParams {
     // untransformed combination sum_l a_kl x_l
     long long jstride;
     KCoef Acomb[IRK_MAX_S * IRK_MAX_S];
+    // row counter of the kernels that hand out element rows dynamically
+    // (zeroed by their launcher before each launch)
+    int *rowctr;
 };
 
 // Columns after which every double-float accumulator of the operator product

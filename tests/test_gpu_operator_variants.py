@@ -23,7 +23,7 @@ from _parity import rel
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-N_VARIANTS = 17
+N_VARIANTS = 19
 
 
 def dev(a):
@@ -56,11 +56,11 @@ def test_operator_variants_bitwise_equal(krylov, kind, s, m):
     assert rel(outs[0], y_ref) <= 1e-13
 
 
-@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16])
+@pytest.mark.parametrize("variant", [4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15, 16, 17, 18])
 def test_solve_with_pipelined_product_is_bitwise_equal(variant):
     """The residual form (y = rhs - B x) of the pipelined kernel, inside a
     full preconditioned solve: same W and iteration count as variant 0.
-    The compile-time variants (7, 9-16) there also take the kernels that
+    The compile-time variants (7, 9-18) there also take the kernels that
     skip the zero low words of binary32 preconditioned vectors."""
     from paper_1701_07181_gb300 import irk
     P = make("2d", 3, 40)
