@@ -283,8 +283,9 @@ __global__ void __launch_bounds__(TpShape<S, B, CK, NU, R, GO, PW>::THREADS,
 }
 
 // k_matvec_tp with the element rows handed out at run time: each producer
-// lane takes its group's next row from a global counter (one row ahead of
-// the one it streams), so that every group keeps working until the rows run
+// lane takes its group's next row from a global counter (zeroed by the
+// launcher; one row ahead of the one it streams), so that every group keeps
+// working until the rows run
 // out instead of a fixed share of rows leaving a tail of groups with one row
 // more than the others.  The producer writes each row's index and block
 // count into a two-entry table of its group before the row's first unit; the
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(TpShape<S, B, CK, NU, R, GO, PW>::THREADS,
 // "full" arrival that carries no copy, ends the group.  The table entry of a
 // row is rewritten two rows later, by which time its consumers have moved on
 // (a row spans more units than the ring holds).  Same accumulation order as
-// every other variant.
+// every other variant; waits bounded as in k_matvec_tp.
 template <int S, int B, bool XF, int CK, int NU, int R, int GO, int MB>
 __global__ void __launch_bounds__(TpShape<S, B, CK, NU, R, GO, 1>::THREADS, MB)
     k_matvec_tpd(MatvecParams P, int *err) {
