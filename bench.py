@@ -246,6 +246,7 @@ def run_reference(args):
             "data": "synthetic", "config": arm_config(world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
                              "cpu_model": model, "host_cores": cores},
+            "solves_per_step": 1,  # one complete solve per step (the GPU arm's step has one per dt)
             "iters_per_solve": its[: len(DTS)],
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
